@@ -1,0 +1,240 @@
+"""CPU oracle for exact k-clique counting -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The CUDA library never loads it and
+shares no code with it (``kc_oracle.c`` is plain sequential C).
+
+Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
+
+* ``count`` / ``count_per_vertex``: brute force over all k-subsets (n <= 30),
+  C(n,k) on K_n, elementary symmetric polynomials on Turan graphs,
+  trace(A^3)/6 and diag(A^3)/2 for triangles, additivity over disjoint unions,
+  invariance over four orderings and random relabellings, sum of per-vertex
+  counts = k * total, k=1 -> n, k=2 -> m, bipartite -> 0, planted disjoint
+  cliques, and the 4-clique fragment of the paper's worked example
+  (Appendix A, Figure 7; the figure itself is missing, so that pin is partial).
+* ``count_arc``: sums over all arcs equal ``count`` (k >= 2).
+* ``orient`` (degree / degeneracy / original / gp): every ordering yields an
+  acyclic orientation that keeps each edge once; the degree and GP orders
+  are checked against their defining properties on hand-made graphs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libkcoracle.so")
+_SRC = os.path.join(_HERE, "kc_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ERANGE, ENOMEM = 0, 1, 2, 3
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+class OracleOverflow(OracleError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            u32, i64, cint = ctypes.c_uint32, ctypes.c_int64, ctypes.c_int
+            lib.or_rank_degree.argtypes = [u32, P, P]
+            lib.or_rank_degeneracy.argtypes = [u32, P, P, P]
+            lib.or_rank_gp.argtypes = [u32, P, P, P, P, P]
+            lib.or_direct.argtypes = [u32, P, P, P, P, P]
+            lib.or_direct.restype = i64
+            lib.or_count.argtypes = [u32, P, P, cint, u32, u32, P, P, P]
+            lib.or_count_arc.argtypes = [u32, P, P, cint, u32, u32, P, P]
+            lib.or_brute.argtypes = [u32, P, cint, P, P]
+            for f in (lib.or_rank_degree, lib.or_rank_degeneracy, lib.or_rank_gp, lib.or_count,
+                      lib.or_count_arc, lib.or_brute):
+                f.restype = cint
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _check(rc: int):
+    if rc == ERANGE:
+        raise OracleOverflow("count does not fit in uint64")
+    if rc != OK:
+        raise OracleError(f"oracle status {rc}")
+
+
+@dataclass
+class Dag:
+    """Oriented graph: ``ptr`` uint64[n+1], ``adj`` uint32[m] (out-lists, ascending id)."""
+    n: int
+    ptr: np.ndarray
+    adj: np.ndarray
+    rank: np.ndarray
+
+    @property
+    def m(self) -> int:
+        return int(self.ptr[-1])
+
+
+def _csr_arrays(g):
+    return (np.ascontiguousarray(g.row_ptr, dtype=np.uint64), np.ascontiguousarray(g.col, dtype=np.uint32))
+
+
+def rank(g, method: str = "degree", perm=None) -> np.ndarray:
+    """Position of every vertex in the chosen total order.
+
+    methods: "degree" (non-decreasing degree, ties by id), "degeneracy"
+    (Matula-Beck k-core order), "original" (ids), "gp" (Goodrich-Pszona,
+    Algorithm 3 with epsilon = 1), "perm" (the given ranks).
+    """
+    lib = _load()
+    rp, col = _csr_arrays(g)
+    r = np.empty(max(g.n, 1), dtype=np.uint32)
+    if method == "degree":
+        _check(lib.or_rank_degree(g.n, _p(rp), _p(r)))
+    elif method == "degeneracy":
+        _check(lib.or_rank_degeneracy(g.n, _p(rp), _p(col), _p(r)))
+    elif method == "original":
+        r[:g.n] = np.arange(g.n, dtype=np.uint32)
+    elif method == "gp":
+        _check(lib.or_rank_gp(g.n, _p(rp), _p(col), _p(r), None, None))
+    elif method == "perm":
+        r[:g.n] = np.asarray(perm, dtype=np.uint32)
+    else:
+        raise ValueError(method)
+    return r[:g.n]
+
+
+def gp_rounds(g):
+    """(rank, round, induced degree at removal) of the Goodrich-Pszona order."""
+    lib = _load()
+    rp, col = _csr_arrays(g)
+    r = np.empty(max(g.n, 1), dtype=np.uint32)
+    rd = np.empty(max(g.n, 1), dtype=np.uint32)
+    dg = np.empty(max(g.n, 1), dtype=np.uint32)
+    _check(lib.or_rank_gp(g.n, _p(rp), _p(col), _p(r), _p(rd), _p(dg)))
+    return r[:g.n], rd[:g.n], dg[:g.n]
+
+
+def orient(g, method: str = "degree", perm=None) -> Dag:
+    """Direct every edge from the lower to the higher vertex of the order."""
+    lib = _load()
+    rp, col = _csr_arrays(g)
+    r = np.ascontiguousarray(rank(g, method, perm), dtype=np.uint32)
+    ptr = np.empty(g.n + 1, dtype=np.uint64)
+    adj = np.empty(max(g.nnz // 2, 1), dtype=np.uint32)
+    m = lib.or_direct(g.n, _p(rp), _p(col), _p(r), _p(ptr), _p(adj))
+    return Dag(g.n, ptr, adj[:m].copy(), r)
+
+
+def _count_range(dag: Dag, k: int, lo: int, hi: int, pv):
+    lib = _load()
+    slo = ctypes.c_uint64()
+    shi = ctypes.c_uint64()
+    adj = dag.adj if dag.adj.size else np.zeros(1, np.uint32)
+    rc = lib.or_count(dag.n, _p(dag.ptr), _p(adj), k, lo, hi, ctypes.byref(slo), ctypes.byref(shi),
+                      None if pv is None else _p(pv))
+    return rc, (shi.value << 64) | slo.value
+
+
+def count(dag: Dag, k: int, threads: int = 1, lo: int = 0, hi: int | None = None) -> int:
+    """Number of k-cliques (Algorithm 1 from every root in [lo, hi)). Raises on uint64 overflow."""
+    hi = dag.n if hi is None else hi
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    if threads <= 1:
+        rc, t = _count_range(dag, k, lo, hi, None)
+        _check(rc)
+    else:
+        bounds = np.linspace(lo, hi, threads * 8 + 1).astype(np.int64)
+        with ThreadPoolExecutor(threads) as ex:
+            res = list(ex.map(lambda ab: _count_range(dag, k, int(ab[0]), int(ab[1]), None),
+                              zip(bounds[:-1], bounds[1:])))
+        for rc, _ in res:
+            _check(rc)
+        t = sum(x for _, x in res)
+    if t >= 1 << 64:
+        raise OracleOverflow("count does not fit in uint64")
+    return int(t)
+
+
+def count_per_vertex(dag: Dag, k: int) -> tuple[int, np.ndarray]:
+    """(total, per-vertex counts): pv[v] = number of k-cliques containing v."""
+    pv = np.zeros(max(dag.n, 1), dtype=np.uint64)
+    rc, t = _count_range(dag, k, 0, dag.n, pv)
+    _check(rc)
+    if t >= 1 << 64:
+        raise OracleOverflow("count does not fit in uint64")
+    return int(t), pv[:dag.n]
+
+
+def count_arc(dag: Dag, k: int, u: int, v: int) -> int:
+    """k-cliques whose two lowest vertices in the order are the arc u->v."""
+    lib = _load()
+    slo = ctypes.c_uint64()
+    shi = ctypes.c_uint64()
+    adj = dag.adj if dag.adj.size else np.zeros(1, np.uint32)
+    _check(lib.or_count_arc(dag.n, _p(dag.ptr), _p(adj), k, u, v, ctypes.byref(slo), ctypes.byref(shi)))
+    t = (shi.value << 64) | slo.value
+    if t >= 1 << 64:
+        raise OracleOverflow("count does not fit in uint64")
+    return int(t)
+
+
+def brute(g, k: int) -> tuple[int, np.ndarray]:
+    """Enumerate all k-subsets (the definition of a k-clique); for n <= ~30."""
+    lib = _load()
+    from_csr = np.zeros((g.n, g.n), dtype=np.uint8)
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr).astype(np.int64))
+    from_csr[src, g.col.astype(np.int64)] = 1
+    tot = ctypes.c_uint64()
+    pv = np.zeros(max(g.n, 1), dtype=np.uint64)
+    _check(lib.or_brute(g.n, _p(from_csr), k, ctypes.byref(tot), _p(pv)))
+    return int(tot.value), pv[:g.n]
+
+
+def timed_count(g, k: int, threads: int, method: str = "degree", max_seconds: float | None = None):
+    """Orient + count as in the paper's timing (orientation included, load excluded).
+
+    Returns (total, seconds, roots_done). With max_seconds the roots are taken in
+    slices until the budget is spent, so the caller can scale a bounded sample.
+    """
+    t0 = time.perf_counter()
+    dag = orient(g, method)
+    if max_seconds is None:
+        tot = count(dag, k, threads=threads)
+        return tot, time.perf_counter() - t0, dag.n
+    tot, done = 0, 0
+    step = max(1, dag.n // 256)
+    while done < dag.n and time.perf_counter() - t0 < max_seconds:
+        hi = min(dag.n, done + step)
+        tot += count(dag, k, threads=threads, lo=done, hi=hi)
+        done = hi
+    return tot, time.perf_counter() - t0, done
