@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark: exact k-clique counting (arb-count) on R-MAT scale 20 on one GB300.
+
+Workload: R-MAT with 2^20 vertices and 16 * 2^20 sampled pairs,
+(a, b, c, d) = (0.57, 0.19, 0.19, 0.05), seed 2, symmetrised, deduplicated,
+self-loops dropped, ids permuted (synthetic stand-in for the paper's SNAP
+graphs). One step = orient (degree order) + per-vertex and total counts for
+k = 4, 5, 6, 7. Metric: k-cliques counted per second (sum over the four k of
+the totals, divided by the step time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank runs an
+independent replica on its own GPU (weak scaling, no collective on the data
+path); value = all ranks' cliques / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "k-cliques counted/sec"
+UNIT = "cliques/s"
+WORKLOAD = "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 2; k=4,5,6,7 total + per-vertex"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ks", default="4,5,6,7")
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def make_graph(scale: int):
+    from paper_2002_10047_gb300 import graphgen as gg
+    return gg.rmat(scale, 16, 0.57, 0.19, 0.19, seed=2, permute=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.t:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_rate(g, ks, seconds: float, threads: int):
+    """Oracle (orient + per-vertex count) on a bounded sample of roots: the first r
+    vertex ids of the permuted graph (a uniform random sample of roots), grown until
+    the time budget is spent; orientation time is scaled to the sample."""
+    import oracle
+    t0 = time.perf_counter()
+    dag = oracle.orient(g, "degree")
+    t_orient = time.perf_counter() - t0
+    per_k = seconds / len(ks)
+    cliques, t_total, desc = 0, 0.0, []
+    for k in ks:
+        done, tot, tk = 0, 0, 0.0
+        step = max(256, g.n // 4096)
+        while done < g.n and tk < per_k:
+            hi = min(g.n, done + step)
+            sub = oracle.Dag(dag.n, dag.ptr, dag.adj, dag.rank)
+            ta = time.perf_counter()
+            tot += _count_pv_range(sub, k, done, hi, threads)
+            tk += time.perf_counter() - ta
+            done = hi
+            step *= 2
+        frac = done / g.n
+        cliques += tot
+        t_total += tk + t_orient * frac
+        desc.append(f"k={k}: roots [0,{done}) of {g.n} ({100 * frac:.2f}%)")
+    return cliques / t_total, cliques, t_total, "; ".join(desc)
+
+
+def _count_pv_range(dag, k, lo, hi, threads):
+    """Per-vertex oracle over roots [lo, hi) split across threads (own arrays, summed)."""
+    import ctypes
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    bounds = np.linspace(lo, hi, threads + 1).astype(np.int64)
+
+    def work(i):
+        pv = np.zeros(dag.n, dtype=np.uint64)
+        rc, t = oracle._count_range(dag, k, int(bounds[i]), int(bounds[i + 1]), pv)
+        oracle._check(rc)
+        return t
+
+    with ThreadPoolExecutor(threads) as ex:
+        return sum(ex.map(work, range(threads)))
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ks = [int(x) for x in args.ks.split(",")]
+    g = make_graph(args.scale)
+    cores = host_cores()
+    budget = max(2.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        rate, _, _, desc = oracle_rate(g, ks, budget, cores)
+        if i >= args.warmup:
+            rates.append(rate)
+    v = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "orientation": "degree"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {desc}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_10047_gb300 import build as kbuild
+    kbuild.build()
+    from paper_2002_10047_gb300 import kclique as kc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ks = [int(x) for x in args.ks.split(",")]
+    g = make_graph(args.scale)
+    rp, col = kc.csr_to_device(g, dev)
+    n = g.n
+    stream = torch.cuda.current_stream()
+    pv_buf = torch.empty(n, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step(ev=None):
+        totals = {}
+        if ev is not None:
+            ev["orient"][0].record(stream)
+        dag = kc.orient(rp, col, n, method="degree")
+        if ev is not None:
+            ev["orient"][1].record(stream)
+        for k in ks:
+            if ev is not None:
+                ev[k][0].record(stream)
+            t, _ = kc.count_per_vertex(dag, k, out=pv_buf)
+            if ev is not None:
+                ev[k][1].record(stream)
+            totals[k] = t
+        dag.free()
+        return totals
+
+    def new_events():
+        e = {"orient": (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))}
+        for k in ks:
+            e[k] = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        return e
+
+    for _ in range(args.warmup):
+        totals = step()
+    torch.cuda.synchronize()
+
+    launches0 = kc.kc_kernel_launches()
+    step_ms, per_k_ms, orient_ms = [], {k: [] for k in ks}, []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between steps, outside the step's events
+            ev = new_events()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            totals = step(ev)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            orient_ms.append(ev["orient"][0].elapsed_time(ev["orient"][1]))
+            for k in ks:
+                per_k_ms[k].append(ev[k][0].elapsed_time(ev[k][1]))
+        torch.cuda.synchronize()
+        barrier()
+    launches = (kc.kc_kernel_launches() - launches0) // max(1, args.steps)
+    t_step = sum(step_ms) / len(step_ms)
+    t_max = t_step
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    cliques = sum(totals.values())
+    value = cliques * world / (t_max / 1e3)
+
+    # ---- end to end through host buffers (pinned), same metric
+    e2e = None
+    if not args.no_e2e:
+        h_rp = torch.from_numpy(g.row_ptr.astype(np.int64)).pin_memory()
+        h_col = torch.from_numpy(g.col.view(np.int32)).pin_memory()
+        h_pv = torch.empty(n, dtype=torch.int64).pin_memory()
+        d_rp = torch.empty_like(rp)
+        d_col = torch.empty_like(col)
+        h2d = h_rp.numel() * 8 + h_col.numel() * 4
+        d2h = len(ks) * n * 8
+
+        def e2e_step():
+            d_rp.copy_(h_rp, non_blocking=True)
+            d_col.copy_(h_col, non_blocking=True)
+            dag = kc.orient(d_rp, d_col, n, method="degree")
+            tot = 0
+            for k in ks:
+                t, _ = kc.count_per_vertex(dag, k, out=pv_buf)
+                h_pv.copy_(pv_buf, non_blocking=True)
+                tot += t
+            torch.cuda.current_stream().synchronize()
+            dag.free()
+            return tot
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tot = e2e_step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        te = sum(times) / len(times)
+        e2e = {"value": tot * world / (te / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": te}
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel (the count pass with the largest time)
+    import json as _json
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = _json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dag = kc.orient(rp, col, n, method="degree")
+    st = kc.dag_stats(dag)
+    m = dag.m
+    dag.free()
+    # algorithmic bytes of one counting pass (first-level induced subgraphs, Section 3.3):
+    # root offsets + root list + out-neighbour offsets + out-neighbour lists + per-vertex output
+    b_count = 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * st["sum_arc_head"] + 8 * n
+    per_k = {}
+    for k in ks:
+        ms = sum(per_k_ms[k]) / len(per_k_ms[k])
+        per_k[str(k)] = {"cliques": totals[k], "ms": ms, "cliques_per_s": totals[k] / (ms / 1e3),
+                         "alg_gbs": b_count / (ms / 1e3) / 1e9}
+    dom = max(ks, key=lambda k: per_k[str(k)]["ms"])
+    achieved = per_k[str(dom)]["alg_gbs"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "orientation": "degree",
+                   "l2": "flushed between steps (512 MiB write, outside step events)",
+                   "parallelism": f"replicas x{world}"},
+        "per_k": per_k, "orient_ms": sum(orient_ms) / len(orient_ms),
+        "roofline": {"bound": "hbm", "kernel": f"count_kernel k={dom}", "achieved": achieved,
+                     "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "alg_bytes_per_launch": b_count},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        cores = host_cores()
+        rate, cl, secs, desc = oracle_rate(g, ks, args.cpu_seconds, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc, "seconds": secs}
+    out = json.dumps(line)
+    print(out, flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(out + "\n")
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * kclique.h -- C ABI of libkclique.so: exact k-clique counting on a low
+ * out-degree orientation (the arb-count method of Shi, Dhulipala and Shun,
+ * "Parallel Clique Counting and Peeling Algorithms", Section 3), on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* are device pointers on the current CUDA device;
+ *    pointers named h_* are host pointers. The library never frees a
+ *    caller's buffer.
+ *  - All device work is enqueued on the caller's stream `stream` (0 = the
+ *    legacy default stream). Entry points that return a host value
+ *    synchronise that stream before returning.
+ *  - Every entry point returns a kc_status. Nothing throws or aborts across
+ *    the boundary; CUDA errors are reported as KC_ECUDA (the CUDA error string
+ *    is available from kc_last_cuda_error()).
+ *  - Counts are exact unsigned 64-bit integers. A count that does not fit is
+ *    reported as KC_ERANGE, never wrapped.
+ *  - Thread safety: distinct kc_dag handles may be used concurrently from
+ *    different host threads and streams; one handle may be read (counted)
+ *    concurrently, since counting never writes to it.
+ */
+#ifndef KCLIQUE_H
+#define KCLIQUE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *kc_stream_t; /* a cudaStream_t */
+
+typedef enum {
+  KC_OK = 0,
+  KC_EINVAL = 1,    /* bad argument, k out of range, or a malformed CSR */
+  KC_ERANGE = 2,    /* a count does not fit in uint64 */
+  KC_ENOMEM = 3,    /* a device allocation failed */
+  KC_ETIMEDOUT = 4, /* the deadline passed or the cancel flag was raised */
+  KC_ECUDA = 5,     /* a CUDA runtime error; see kc_last_cuda_error() */
+  KC_ECAPACITY = 6  /* a root's out-neighbourhood exceeds KC_MAX_OUT_DEGREE */
+} kc_status;
+
+/* Largest k accepted (k = 1 .. KC_KMAX). */
+#define KC_KMAX 32
+/* Largest out-degree a root may have in the oriented graph. Under the degree
+ * ordering every out-degree is at most sqrt(2m), so this bound is reached only
+ * by graphs with m above ~1.3e8 that also hold a clique-like core of more than
+ * 16384 vertices. */
+#define KC_MAX_OUT_DEGREE 16384
+
+/* Orientation methods (Section 3.1; Section 5, "Algorithm Implementations"). */
+#define KC_ORIENT_DEGREE 0 /* rank by (degree, id), ascending */
+#define KC_ORIENT_GP 1     /* Goodrich-Pszona rounds, Algorithm 3 with epsilon = 1 */
+/* Flags or-ed into `method`: */
+#define KC_VALIDATE_SYMMETRY 0x100 /* also check that every arc u->v has v->u */
+
+/*
+ * Simple undirected graph in CSR form (Section 2, "Graph Storage").
+ *   n        number of vertices (ids 0 .. n-1)
+ *   nnz      number of directed arcs = 2m (each undirected edge twice)
+ *   d_row_ptr device uint64[n+1], d_row_ptr[0] = 0, d_row_ptr[n] = nnz
+ *   d_col    device uint32[nnz], row v = neighbours of v, strictly ascending,
+ *            no self-loops (the paper assumes simple graphs, Section 2)
+ * Borrowed: the library reads it during kc_orient only.
+ */
+typedef struct {
+  uint32_t n;
+  uint64_t nnz;
+  const uint64_t *d_row_ptr;
+  const uint32_t *d_col;
+} kc_csr;
+
+/* Opaque oriented graph (the DAG DG of Algorithm 1) with library-owned device
+ * buffers: out-lists N+(v) (neighbours later in the total order), each sorted
+ * ascending, plus the root work list used by the counting kernels. */
+typedef struct kc_dag kc_dag;
+
+/*
+ * kc_orient -- Orient(G) of Algorithm 1 (Section 3.1): rank the vertices by
+ * the chosen total order and keep each edge as one arc from its lower to its
+ * higher endpoint ("direct the graph in CSR format ... using prefix sum and
+ * filter", end of Section 3.1).
+ *   g       the input CSR (device arrays)
+ *   method  KC_ORIENT_DEGREE or KC_ORIENT_GP, optionally | KC_VALIDATE_SYMMETRY
+ *   out     receives a new handle on success (*out untouched on error)
+ * The CSR is validated first (ascending rows, no self-loops, ids < n,
+ * row_ptr consistent; symmetry on request): a violation gives KC_EINVAL.
+ * Synchronises `stream`. Free the handle with kc_dag_free.
+ */
+kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t stream);
+
+/* Release a handle (stream-ordered on the stream it was created on). NULL is a no-op. */
+void kc_dag_free(kc_dag *d);
+
+/* Vertex count n, arc count m (= undirected edges), largest out-degree. */
+uint32_t kc_dag_n(const kc_dag *d);
+uint64_t kc_dag_m(const kc_dag *d);
+uint32_t kc_dag_max_out_degree(const kc_dag *d);
+
+/*
+ * Copy the oriented graph out (device to device): d_ptr uint64[n+1] and
+ * d_col uint32[m], in the vertex ids of the input CSR. Either may be NULL.
+ * Synchronises `stream`.
+ */
+kc_status kc_dag_export(const kc_dag *d, uint64_t *d_ptr, uint32_t *d_col, kc_stream_t stream);
+
+/*
+ * kc_count -- arb-count(G, k) of Algorithm 1: the number of k-cliques
+ * (Section 2: k vertices with all k(k-1)/2 edges present).
+ *   k        1 .. KC_KMAX (k = 1 gives n, k = 2 gives m)
+ *   h_total  receives the count
+ * Synchronises `stream`. KC_ERANGE if the count does not fit in uint64.
+ */
+kc_status kc_count(const kc_dag *d, int k, uint64_t *h_total, kc_stream_t stream);
+
+/*
+ * kc_count_per_vertex -- arb-count-v (Section 3.2, used by Algorithm 2):
+ * d_out[v] = number of k-cliques that contain v, for every vertex v (so the
+ * entries sum to k times the total).
+ *   d_out    device uint64[n], caller-owned; overwritten
+ *   h_total  optional (NULL allowed): receives the total count
+ * Synchronises `stream`.
+ */
+kc_status kc_count_per_vertex(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_total,
+                              kc_stream_t stream);
+
+/*
+ * kc_count_per_arc -- rooted counts used for sampled parity checks: for the
+ * arc with index e in the exported out-lists (u -> v, e in
+ * [ptr[u], ptr[u+1])), d_out[e] = number of k-cliques whose two lowest
+ * vertices in the total order are u and v (the k-cliques found below that
+ * arc by the recursion of Algorithm 1). k >= 2.
+ *   d_out    device uint64[m], caller-owned; overwritten
+ *   h_total  optional: receives the total count
+ * Synchronises `stream`.
+ */
+kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_total,
+                           kc_stream_t stream);
+
+/*
+ * Work statistics of an oriented graph, used for the bytes a counting pass
+ * must move (computed exactly on the device):
+ *   sum_out_sq     sum over roots u of d+(u)^2
+ *   sum_arc_head   sum over arcs u->v of d+(v) (adjacency read to build the
+ *                  first-level induced subgraphs of Section 3.3)
+ *   triangles      number of 3-cliques
+ *   max_out        largest out-degree
+ */
+typedef struct {
+  uint64_t sum_out_sq;
+  uint64_t sum_arc_head;
+  uint64_t triangles;
+  uint32_t max_out;
+} kc_dag_stats;
+kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t stream);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all entry points, all devices). For accounting in benchmarks. */
+uint64_t kc_kernel_launches(void);
+
+/* Human-readable text for a status code (static storage). */
+const char *kc_strerror(int status);
+/* Text of the last CUDA error seen by this host thread (static per thread). */
+const char *kc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KCLIQUE_H */

@@ -185,11 +185,37 @@ def count(dag: Dag, k: int, threads: int = 1, lo: int = 0, hi: int | None = None
     return int(t)
 
 
-def count_per_vertex(dag: Dag, k: int) -> tuple[int, np.ndarray]:
-    """(total, per-vertex counts): pv[v] = number of k-cliques containing v."""
-    pv = np.zeros(max(dag.n, 1), dtype=np.uint64)
-    rc, t = _count_range(dag, k, 0, dag.n, pv)
-    _check(rc)
+def count_per_vertex(dag: Dag, k: int, threads: int = 1) -> tuple[int, np.ndarray]:
+    """(total, per-vertex counts): pv[v] = number of k-cliques containing v.
+
+    With threads > 1 the roots are split into ranges, each range summed into its
+    own array, and the arrays added (the same sequential routine per range).
+    """
+    if threads <= 1:
+        pv = np.zeros(max(dag.n, 1), dtype=np.uint64)
+        rc, t = _count_range(dag, k, 0, dag.n, pv)
+        _check(rc)
+    else:
+        bounds = np.linspace(0, dag.n, threads * 4 + 1).astype(np.int64)
+        parts = [np.zeros(max(dag.n, 1), dtype=np.uint64) for _ in range(threads)]
+        chunks = list(zip(bounds[:-1], bounds[1:]))
+
+        def work(ti):
+            tot = 0
+            for ci in range(ti, len(chunks), threads):
+                rc, x = _count_range(dag, k, int(chunks[ci][0]), int(chunks[ci][1]), parts[ti])
+                _check(rc)
+                tot += x
+            return tot
+
+        with ThreadPoolExecutor(threads) as ex:
+            t = sum(ex.map(work, range(threads)))
+        pv = parts[0]
+        for q in parts[1:]:
+            s = pv + q
+            if np.any(s < pv):
+                raise OracleOverflow("per-vertex count does not fit in uint64")
+            pv = s
     if t >= 1 << 64:
         raise OracleOverflow("count does not fit in uint64")
     return int(t), pv[:dag.n]

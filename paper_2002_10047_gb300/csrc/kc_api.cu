@@ -1,0 +1,340 @@
+// The C ABI of libkclique.so (declared in include/kclique.h): argument
+// checks, device allocation (stream-ordered), launch orchestration and the
+// mapping of device status words to kc_status codes.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "kc_internal.cuh"
+#include "kc_orient.cuh"
+#include "kclique.h"
+
+struct kc_dag {
+  uint32_t n = 0;
+  uint64_t m = 0;
+  uint32_t max_out = 0;
+  uint64_t *ptr = nullptr;    // n+1
+  uint32_t *col = nullptr;    // m
+  uint32_t *order = nullptr;  // n, roots by out-degree descending
+  std::vector<uint64_t> ge;   // ge[t] = #roots with out-degree >= t, t = 0 .. max_out+1
+  cudaStream_t stream = nullptr;
+  int device = 0;
+};
+
+#include <atomic>
+
+namespace kc {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace kc
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+kc_status cuda_fail(cudaError_t e) {
+  g_cuda_err = cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return KC_ENOMEM;
+  return KC_ECUDA;
+}
+
+#define KC_CK(call)                               \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_);  \
+  } while (0)
+
+// Stream-ordered device buffers released when the scope ends.
+struct DevBuf {
+  void *p = nullptr;
+  cudaStream_t s = nullptr;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, s);
+  }
+  cudaError_t alloc(size_t bytes, cudaStream_t st) {
+    s = st;
+    return cudaMallocAsync(&p, bytes ? bytes : 16, st);
+  }
+  template <typename T>
+  T *as() const {
+    return (T *)p;
+  }
+  void *release() {
+    void *q = p;
+    p = nullptr;
+    return q;
+  }
+};
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kc_strerror(int status) {
+  switch (status) {
+    case KC_OK: return "ok";
+    case KC_EINVAL: return "invalid argument or malformed graph";
+    case KC_ERANGE: return "count does not fit in uint64";
+    case KC_ENOMEM: return "device allocation failed";
+    case KC_ETIMEDOUT: return "deadline passed or cancelled";
+    case KC_ECUDA: return "CUDA runtime error";
+    case KC_ECAPACITY: return "out-degree above KC_MAX_OUT_DEGREE";
+    default: return "unknown status";
+  }
+}
+
+const char *kc_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+uint64_t kc_kernel_launches(void) { return kc::g_launches.load(std::memory_order_relaxed); }
+
+uint32_t kc_dag_n(const kc_dag *d) { return d ? d->n : 0; }
+uint64_t kc_dag_m(const kc_dag *d) { return d ? d->m : 0; }
+uint32_t kc_dag_max_out_degree(const kc_dag *d) { return d ? d->max_out : 0; }
+
+void kc_dag_free(kc_dag *d) {
+  if (!d) return;
+  if (d->ptr) cudaFreeAsync(d->ptr, d->stream);
+  if (d->col) cudaFreeAsync(d->col, d->stream);
+  if (d->order) cudaFreeAsync(d->order, d->stream);
+  delete d;
+}
+
+kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t stream) {
+  if (!g || !out) return KC_EINVAL;
+  const int base = method & 0xff;
+  const int sym = (method & KC_VALIDATE_SYMMETRY) ? 1 : 0;
+  if (base != KC_ORIENT_DEGREE && base != KC_ORIENT_GP) return KC_EINVAL;
+  if ((method & ~(0xff | KC_VALIDATE_SYMMETRY)) != 0) return KC_EINVAL;
+  if (g->n > 0 && (!g->d_row_ptr || (g->nnz > 0 && !g->d_col))) return KC_EINVAL;
+  if (g->nnz % 2 != 0) return KC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t n = g->n;
+
+  kc_dag *D = new kc_dag();
+  D->n = n;
+  D->stream = s;
+  cudaGetDevice(&D->device);
+  struct Guard {
+    kc_dag *d;
+    ~Guard() {
+      if (d) kc_dag_free(d);
+    }
+  } guard{D};
+
+  DevBuf status;
+  KC_CK(status.alloc(sizeof(unsigned) * 2, s));
+  KC_CK(cudaMemsetAsync(status.p, 0, sizeof(unsigned) * 2, s));
+  unsigned h_status[2] = {0, 0};
+  if (n > 0) {
+    KC_CK(kc::launch_validate(*g, sym, status.as<unsigned>(), s));
+    KC_CK(cudaMemcpyAsync(h_status, status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    KC_CK(cudaStreamSynchronize(s));
+    if (h_status[0] & kc::ST_BAD_CSR) return KC_EINVAL;
+  }
+
+  KC_CK(cudaMallocAsync((void **)&D->ptr, sizeof(uint64_t) * ((size_t)n + 1), s));
+  if (n == 0) {
+    KC_CK(cudaMemsetAsync(D->ptr, 0, sizeof(uint64_t), s));
+    KC_CK(cudaMallocAsync((void **)&D->col, 16, s));
+    KC_CK(cudaMallocAsync((void **)&D->order, 16, s));
+    D->ge.assign(2, 0);
+    KC_CK(cudaStreamSynchronize(s));
+    *out = D;
+    guard.d = nullptr;
+    return KC_OK;
+  }
+
+  DevBuf key, outdeg, scan_tmp;
+  KC_CK(key.alloc(sizeof(uint64_t) * n, s));
+  KC_CK(outdeg.alloc(sizeof(uint32_t) * n, s));
+  if (base == KC_ORIENT_DEGREE) {
+    KC_CK(kc::launch_degree_key(*g, key.as<uint64_t>(), s));
+  } else {
+    kc_status st = kc::gp_rank(*g, key.as<uint64_t>(), s);
+    if (st != KC_OK) return st;
+  }
+  unsigned *d_max = status.as<unsigned>() + 1;
+  KC_CK(kc::launch_count_out(*g, key.as<uint64_t>(), outdeg.as<uint32_t>(), d_max, s));
+  const size_t te = kc::scan_tmp_elems(n);
+  KC_CK(scan_tmp.alloc(sizeof(uint64_t) * te, s));
+  KC_CK(kc::exclusive_scan_u32(outdeg.as<uint32_t>(), D->ptr, n, scan_tmp.as<uint64_t>(), te, s));
+  uint64_t h_m = 0;
+  KC_CK(cudaMemcpyAsync(&h_m, D->ptr + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaMemcpyAsync(&h_status[1], d_max, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  // exactly one arc per undirected edge is kept; any other total means the
+  // CSR is not symmetric
+  if (h_m != g->nnz / 2) return KC_EINVAL;
+  D->m = h_m;
+  D->max_out = h_status[1];
+  KC_CK(cudaMallocAsync((void **)&D->col, sizeof(uint32_t) * (h_m ? h_m : 1), s));
+  KC_CK(kc::launch_write_out(*g, key.as<uint64_t>(), D->ptr, D->col, s));
+
+  // roots ordered by out-degree, descending (counting sort)
+  const uint32_t maxd = D->max_out;
+  DevBuf hist;
+  KC_CK(hist.alloc(sizeof(unsigned) * ((size_t)maxd + 1), s));
+  KC_CK(cudaMemsetAsync(hist.p, 0, sizeof(unsigned) * ((size_t)maxd + 1), s));
+  KC_CK(kc::launch_outdeg_hist(D->ptr, n, hist.as<unsigned>(), maxd, s));
+  std::vector<unsigned> h_hist((size_t)maxd + 1);
+  KC_CK(cudaMemcpyAsync(h_hist.data(), hist.p, sizeof(unsigned) * h_hist.size(), cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  D->ge.assign((size_t)maxd + 2, 0);
+  for (int64_t t = maxd; t >= 0; --t) D->ge[t] = D->ge[t + 1] + h_hist[t];
+  std::vector<unsigned> start((size_t)maxd + 1);
+  for (uint32_t t = 0; t <= maxd; ++t) start[t] = (unsigned)D->ge[t + 1];
+  KC_CK(cudaMemcpyAsync(hist.p, start.data(), sizeof(unsigned) * start.size(), cudaMemcpyHostToDevice, s));
+  KC_CK(cudaMallocAsync((void **)&D->order, sizeof(uint32_t) * n, s));
+  KC_CK(kc::launch_outdeg_scatter(D->ptr, n, hist.as<unsigned>(), maxd, D->order, s));
+  KC_CK(cudaStreamSynchronize(s));  // `start` is a pageable host buffer read by the copy above
+  *out = D;
+  guard.d = nullptr;
+  return KC_OK;
+}
+
+kc_status kc_dag_export(const kc_dag *d, uint64_t *d_ptr, uint32_t *d_col, kc_stream_t stream) {
+  if (!d) return KC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (d_ptr) KC_CK(cudaMemcpyAsync(d_ptr, d->ptr, sizeof(uint64_t) * ((size_t)d->n + 1), cudaMemcpyDeviceToDevice, s));
+  if (d_col && d->m) KC_CK(cudaMemcpyAsync(d_col, d->col, sizeof(uint32_t) * d->m, cudaMemcpyDeviceToDevice, s));
+  KC_CK(cudaStreamSynchronize(s));
+  return KC_OK;
+}
+
+kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t stream) {
+  if (!d || !h_stats) return KC_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf acc;
+  KC_CK(acc.alloc(sizeof(unsigned long long) * 3, s));
+  KC_CK(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 3, s));
+  if (d->n) KC_CK(kc::launch_dag_stats(d->ptr, d->col, d->n, acc.as<unsigned long long>(), s));
+  unsigned long long h[3];
+  KC_CK(cudaMemcpyAsync(h, acc.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  h_stats->sum_out_sq = h[0];
+  h_stats->sum_arc_head = h[1];
+  h_stats->triangles = h[2];
+  h_stats->max_out = d->max_out;
+  return KC_OK;
+}
+
+}  // extern "C"
+
+namespace kc {
+
+// Shared driver of kc_count / kc_count_per_vertex / kc_count_per_arc.
+kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned long long *pa, uint64_t *h_total,
+                    uint64_t deadline_ns, cudaStream_t s) {
+  if (!d || k < 1 || k > KC_KMAX) return KC_EINVAL;
+  if (pa && k < 2) return KC_EINVAL;
+  const uint32_t n = d->n;
+  if (pv) KC_CK(cudaMemsetAsync(pv, 0, sizeof(unsigned long long) * n, s));
+  if (pa && d->m) KC_CK(cudaMemsetAsync(pa, 0, sizeof(unsigned long long) * d->m, s));
+  if (k == 1) {
+    if (pv) KC_CK(launch_fill_u64(pv, n, 1ull, s));
+    KC_CK(cudaStreamSynchronize(s));
+    if (h_total) *h_total = n;
+    return KC_OK;
+  }
+  if (k == 2) {
+    if (pv && n) KC_CK(launch_degree_from_dag(d->ptr, d->col, n, pv, s));
+    if (pa) KC_CK(launch_fill_u64(pa, d->m, 1ull, s));
+    KC_CK(cudaStreamSynchronize(s));
+    if (h_total) *h_total = d->m;
+    return KC_OK;
+  }
+  const uint32_t need = (uint32_t)(k - 1);  // a root needs k-1 out-neighbours
+  if (need > d->max_out) {
+    KC_CK(cudaStreamSynchronize(s));
+    if (h_total) *h_total = 0;
+    return KC_OK;
+  }
+  if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
+  const bool bpv = pv != nullptr, bpa = pa != nullptr;
+
+  // shared-memory budget for a block-level root: keep two blocks per SM
+  const size_t light_bytes = (size_t)kWarps * light_slot_bytes(bpv, bpa);
+  const size_t heavy_budget = 100 * 1024;
+  uint32_t dsmem = kLightMax;
+  while (dsmem < 2048 && root_bytes(dsmem + 1, bpv, bpa) <= heavy_budget) ++dsmem;
+  const size_t smem = std::max(light_bytes, root_bytes(dsmem, bpv, bpa));
+  KC_CK(set_count_smem(bpv, bpa, smem));
+  int per_sm = count_blocks_per_sm(bpv, bpa, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int grid = sm_count() * per_sm;
+
+  CountArgs a;
+  memset(&a, 0, sizeof a);
+  a.ptr = d->ptr;
+  a.col = d->col;
+  a.order = d->order;
+  a.k = k;
+  a.dsmem = dsmem;
+  auto ge = [&](uint64_t t) -> uint32_t { return t < d->ge.size() ? (uint32_t)d->ge[t] : 0u; };
+  a.n_light_end = ge(need);
+  a.n_heavy_end = ge(kLightMax + 1);
+  a.n_huge = ge((uint64_t)dsmem + 1);
+  a.pv = pv;
+  a.pa = pa;
+  a.deadline_ns = deadline_ns;
+
+  DevBuf work, scratch;
+  KC_CK(work.alloc(64, s));
+  KC_CK(cudaMemsetAsync(work.p, 0, 64, s));
+  a.total = work.as<unsigned long long>();
+  a.status = (unsigned *)(work.as<uint8_t>() + 8);
+  a.queue = (unsigned *)(work.as<uint8_t>() + 16);
+  if (a.n_huge > 0) {
+    const size_t slab = (root_bytes(d->max_out, bpv, bpa) + 255) & ~(size_t)255;
+    const size_t budget = (size_t)4 << 30;
+    size_t nb = std::max<size_t>(1, budget / slab);
+    nb = std::min<size_t>(nb, (size_t)grid);
+    nb = std::min<size_t>(nb, (size_t)a.n_huge);
+    KC_CK(scratch.alloc(slab * nb, s));
+    a.scratch = scratch.as<uint64_t>();
+    a.scratch_stride = slab;
+    a.scratch_blocks = (uint32_t)nb;
+  }
+  KC_CK(launch_count(a, bpv, bpa, grid, smem, s));
+  unsigned long long h[2] = {0, 0};
+  KC_CK(cudaMemcpyAsync(h, work.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  const unsigned st = (unsigned)h[1];
+  if (st & ST_CAPACITY) return KC_ECAPACITY;
+  if (st & ST_OVERFLOW) return KC_ERANGE;
+  if (st & ST_TIMEOUT) return KC_ETIMEDOUT;
+  if (h_total) *h_total = h[0];
+  return KC_OK;
+}
+
+}  // namespace kc
+
+extern "C" {
+
+kc_status kc_count(const kc_dag *d, int k, uint64_t *h_total, kc_stream_t stream) {
+  if (!h_total) return KC_EINVAL;
+  return kc::run_count(d, k, nullptr, nullptr, h_total, 0, (cudaStream_t)stream);
+}
+
+kc_status kc_count_per_vertex(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_total, kc_stream_t stream) {
+  if (!d_out) return KC_EINVAL;
+  return kc::run_count(d, k, (unsigned long long *)d_out, nullptr, h_total, 0, (cudaStream_t)stream);
+}
+
+kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_total, kc_stream_t stream) {
+  if (!d_out) return KC_EINVAL;
+  return kc::run_count(d, k, nullptr, (unsigned long long *)d_out, h_total, 0, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,25 @@
+// Launchers of the orientation-side kernels (kc_orient.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kclique.h"
+
+namespace kc {
+cudaError_t launch_validate(const kc_csr &g, int sym, unsigned *status, cudaStream_t s);
+cudaError_t launch_degree_key(const kc_csr &g, uint64_t *key, cudaStream_t s);
+cudaError_t launch_count_out(const kc_csr &g, const uint64_t *key, uint32_t *outdeg, unsigned *maxdeg,
+                             cudaStream_t s);
+cudaError_t launch_write_out(const kc_csr &g, const uint64_t *key, const uint64_t *dag_ptr, uint32_t *dag_col,
+                             cudaStream_t s);
+cudaError_t launch_outdeg_hist(const uint64_t *dp, uint32_t n, unsigned *hist, uint32_t maxd, cudaStream_t s);
+cudaError_t launch_outdeg_scatter(const uint64_t *dp, uint32_t n, unsigned *cursor, uint32_t maxd, uint32_t *order,
+                                  cudaStream_t s);
+cudaError_t launch_fill_u64(unsigned long long *out, size_t n, unsigned long long v, cudaStream_t s);
+cudaError_t launch_degree_from_dag(const uint64_t *dp, const uint32_t *dc, uint32_t n, unsigned long long *out,
+                                   cudaStream_t s);
+// Goodrich-Pszona order keys (kc_gp.cu): okey[v] = round << 32 | degree at removal
+kc_status gp_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s);
+cudaError_t launch_dag_stats(const uint64_t *dp, const uint32_t *dc, uint32_t n, unsigned long long *acc,
+                             cudaStream_t s);
+}  // namespace kc

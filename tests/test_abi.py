@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+entry point declared in include/kclique.h (no compute calls here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(kc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2002_10047_gb300 import build
+    return build.build()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("kc_orient", "kc_count", "kc_count_per_vertex", "kc_count_per_arc", "kc_dag_free",
+                 "kc_dag_n", "kc_dag_m", "kc_strerror", "kc_dag_export", "kc_dag_get_stats"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (kc_\w+)", out))
+    assert declared_functions() <= exported
+
+
+def test_status_strings_without_gpu(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.kc_strerror.restype = ctypes.c_char_p
+    for code in range(7):
+        assert lib.kc_strerror(code)
+    lib.kc_kernel_launches.restype = ctypes.c_uint64
+    assert lib.kc_kernel_launches() == 0
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2002_10047_gb300 import build, kclique
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(kclique, "_lib", None)
+    with pytest.raises(RuntimeError):
+        kclique._load()
