@@ -262,17 +262,21 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
   }
   if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
   const bool bpv = pv != nullptr, bpa = pa != nullptr;
+  const bool colT = bpv && k >= 4;
 
-  // shared-memory budget for a block-level root: keep two blocks per SM
-  const size_t light_bytes = (size_t)kWarps * light_slot_bytes(bpv, bpa);
-  const size_t heavy_budget = 100 * 1024;
-  uint32_t dsmem = kLightMax;
-  while (dsmem < 2048 && root_bytes(dsmem + 1, bpv, bpa) <= heavy_budget) ++dsmem;
-  const size_t smem = std::max(light_bytes, root_bytes(dsmem, bpv, bpa));
-  KC_CK(set_count_smem(bpv, bpa, smem));
-  int per_sm = count_blocks_per_sm(bpv, bpa, smem);
-  if (per_sm < 1) per_sm = 1;
-  const int grid = sm_count() * per_sm;
+  // shared memory of a block root: per-warp item slots + the root's matrix
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t budget = (size_t)(optin > 4096 ? optin - 2048 : 48 * 1024);
+  const uint32_t dcap = block_root_capacity(budget, bpv, bpa, colT);
+  const uint32_t dsmem = std::min<uint32_t>(dcap, std::max<uint32_t>(d->max_out, kLightMax + 1));
+  const size_t block_smem = block_root_smem(dsmem, bpv, bpa, colT);
+  int per_sm_b = 0, per_sm_w = 0;
+  KC_CK(count_occupancy(bpv, bpa, block_smem, &per_sm_b, &per_sm_w));
+  const int sms = sm_count();
+  const int block_grid = sms * std::max(1, per_sm_b);
+  const int warp_grid = sms * std::max(1, per_sm_w);
 
   CountArgs a;
   memset(&a, 0, sizeof a);
@@ -280,11 +284,10 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
   a.col = d->col;
   a.order = d->order;
   a.k = k;
-  a.dsmem = dsmem;
   auto ge = [&](uint64_t t) -> uint32_t { return t < d->ge.size() ? (uint32_t)d->ge[t] : 0u; };
   a.n_light_end = ge(need);
-  a.n_heavy_end = ge(kLightMax + 1);
-  a.n_huge = ge((uint64_t)dsmem + 1);
+  a.n_big = ge(kLightMax + 1);
+  a.n_scratch = ge((uint64_t)dcap + 1);
   a.pv = pv;
   a.pa = pa;
   a.deadline_ns = deadline_ns;
@@ -295,18 +298,18 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
   a.total = work.as<unsigned long long>();
   a.status = (unsigned *)(work.as<uint8_t>() + 8);
   a.queue = (unsigned *)(work.as<uint8_t>() + 16);
-  if (a.n_huge > 0) {
-    const size_t slab = (root_bytes(d->max_out, bpv, bpa) + 255) & ~(size_t)255;
-    const size_t budget = (size_t)4 << 30;
-    size_t nb = std::max<size_t>(1, budget / slab);
-    nb = std::min<size_t>(nb, (size_t)grid);
-    nb = std::min<size_t>(nb, (size_t)a.n_huge);
+  if (a.n_scratch > 0) {
+    const size_t slab = (root_layout(d->max_out, bpv, bpa, colT).bytes + 255) & ~(size_t)255;
+    const size_t sbudget = (size_t)4 << 30;
+    size_t nb = std::max<size_t>(1, sbudget / slab);
+    nb = std::min<size_t>(nb, (size_t)block_grid);
+    nb = std::min<size_t>(nb, (size_t)a.n_scratch);
     KC_CK(scratch.alloc(slab * nb, s));
-    a.scratch = scratch.as<uint64_t>();
+    a.scratch = scratch.as<uint8_t>();
     a.scratch_stride = slab;
     a.scratch_blocks = (uint32_t)nb;
   }
-  KC_CK(launch_count(a, bpv, bpa, grid, smem, s));
+  KC_CK(launch_count(a, bpv, bpa, block_grid, warp_grid, block_smem, s));
   unsigned long long h[2] = {0, 0};
   KC_CK(cudaMemcpyAsync(h, work.p, sizeof h, cudaMemcpyDeviceToHost, s));
   KC_CK(cudaStreamSynchronize(s));

@@ -2,7 +2,6 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
-#include <vector>
 
 #include "kclique.h"
 
@@ -16,69 +15,118 @@ enum : unsigned {
   ST_CAPACITY = 8u,   // an internal capacity check failed (the access was skipped)
 };
 
-constexpr int kBlock = 256;              // threads per block of every kernel here
+constexpr int kBlock = 256;              // threads per block of the orientation kernels
 constexpr int kWarps = kBlock / 32;
+constexpr int kRootBlock = 512;          // threads per block of the block-root counting kernel
+constexpr int kRootWarps = kRootBlock / 32;
 constexpr int kLightMax = 64;            // roots with d+ <= 64 use one warp and one-word rows
 constexpr int kMaxFrames = KC_KMAX - 2;  // depth of the explicit DFS stack
+constexpr int kCompactMax = 128;         // largest candidate set compacted to local ids
+constexpr int kCompactWords = 32;        // compaction needs the root's rows to fit 32 words (d+ <= 2048)
+
+__host__ __device__ inline uint32_t words_of(uint32_t d) { return (d + 63u) / 64u; }
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline uint32_t hash_slots(uint32_t d) {
+  uint32_t t = 64;
+  while (t < 2 * d) t <<= 1;
+  return t;
+}
+
+// Per-root working set of a block-level root with out-degree d:
+//   L      uint32[d]        N+(u)
+//   hkey   uint32[T]        open-addressing table: vertex id -> position in L
+//   hpos   uint16[T]
+//   rows   uint64[d*W]      the induced subgraph on N+(u), row i = N+(L[i]) within N+(u)
+//   colT   uint64[d*W]      transposed rows (per-vertex counts, k >= 4)
+//   cnt    uint64[d]        per-vertex counters (per-vertex only)
+//   asub   uint64[d]        per-arc sums (per-arc only)
+//   pre    uint32[d+1]      prefix of split-arc sizes (k >= 5)
+struct RootLayout {
+  size_t L, hkey, hpos, rows, colT, cnt, asub, pre, bytes;
+};
+__host__ __device__ inline RootLayout root_layout(uint32_t d, bool pv, bool pa, bool colT) {
+  RootLayout o;
+  const uint32_t W = words_of(d), T = hash_slots(d);
+  size_t off = 0;
+  o.L = off; off += align16((size_t)d * 4);
+  o.hkey = off; off += align16((size_t)T * 4);
+  o.hpos = off; off += align16((size_t)T * 2);
+  o.rows = off; off += align16((size_t)d * W * 8);
+  o.colT = off; if (colT) off += align16((size_t)d * W * 8);
+  o.cnt = off; if (pv) off += align16((size_t)d * 8);
+  o.asub = off; if (pa) off += align16((size_t)d * 8);
+  o.pre = off; off += align16(((size_t)d + 1) * 4);
+  o.bytes = off;
+  return o;
+}
+
+// Per-warp slot of the block-root kernel (item scratch): mask words and their
+// prefix counts, the positions of the compacted vertices, the compacted rows
+// and their transpose, and local per-vertex counters.
+struct SlotLayout {
+  size_t mask, pfx, P, S, ST, cs, bytes;
+};
+__host__ __device__ inline SlotLayout slot_layout(bool pv) {
+  SlotLayout o;
+  size_t off = 0;
+  o.mask = off; off += 32 * 8;
+  o.pfx = off; off += 32 * 4;
+  o.P = off; off += align16(kCompactMax * 2);
+  o.S = off; off += kCompactMax * 2 * 8;
+  o.ST = off; if (pv) off += kCompactMax * 2 * 8;
+  o.cs = off; if (pv) off += kCompactMax * 8;
+  o.bytes = align16(off);
+  return o;
+}
+
+// Per-warp slot of the warp-root kernel (roots with d+ <= 64).
+struct LightLayout {
+  size_t L, hkey, hpos, rows, colT, cnt, asub, pre, epre, bytes;
+};
+__host__ __device__ inline LightLayout light_layout(bool pv, bool pa) {
+  LightLayout o;
+  size_t off = 0;
+  o.L = off; off += kLightMax * 4;
+  o.hkey = off; off += 128 * 4;
+  o.hpos = off; off += 128 * 2;
+  o.rows = off; off += kLightMax * 8;
+  o.colT = off; if (pv) off += kLightMax * 8;
+  o.cnt = off; if (pv) off += kLightMax * 8;
+  o.asub = off; if (pa) off += kLightMax * 8;
+  o.pre = off; off += align16((kLightMax + 1) * 4);
+  o.epre = off; off += align16((kLightMax + 1) * 4);
+  o.bytes = align16(off);
+  return o;
+}
 
 struct CountArgs {
   const uint64_t *ptr;       // DAG offsets, n+1
   const uint32_t *col;       // DAG out-lists, m
   const uint32_t *order;     // roots sorted by out-degree, descending
-  uint32_t n_huge;           // order[0, n_huge): d+ > dsmem (matrix in global scratch)
-  uint32_t n_heavy_end;      // order[n_huge, n_heavy_end): kLightMax < d+ <= dsmem (block, smem)
-  uint32_t n_light_end;      // order[n_heavy_end, n_light_end): k-1 <= d+ <= kLightMax (warp)
+  uint32_t n_big;            // order[0, n_big): d+ > kLightMax (block roots)
+  uint32_t n_scratch;        // order[0, n_scratch): block roots whose matrices live in global scratch
+  uint32_t n_light_end;      // order[n_big, n_light_end): k-1 <= d+ <= kLightMax (warp roots)
   int k;
-  uint32_t dsmem;            // largest out-degree whose matrix fits the block's shared memory
   unsigned long long *total; // global sum
   unsigned long long *pv;    // per-vertex output (n) or null
   unsigned long long *pa;    // per-arc output (m) or null
   unsigned *status;
-  unsigned *queue;           // [0] huge, [1] heavy, [2] light
-  uint64_t *scratch;         // huge roots: per-block slabs
+  unsigned *queue;           // [0] scratch roots, [1] shared-memory block roots, [2] warp roots
+  uint8_t *scratch;          // global slabs for roots that do not fit shared memory
   size_t scratch_stride;     // bytes per slab
-  uint32_t scratch_blocks;   // blocks that take huge roots
+  uint32_t scratch_blocks;   // blocks that take scratch roots
   uint64_t deadline_ns;      // globaltimer deadline, 0 = none
 };
-
-// Bytes of the per-root working set for a block-level root with out-degree d
-// (list, rows, transposed rows, per-vertex counters, per-arc sums, pair prefix).
-__host__ __device__ inline size_t root_words(uint32_t d) { return (d + 63u) / 64u; }
-__host__ __device__ inline uint32_t group_for_words(uint32_t w) {
-  uint32_t g = 1;
-  while (g < w && g < 32) g <<= 1;
-  return g;
-}
-// Words per row in memory: the group width G (a power of two >= the row's
-// 64-bit word count) for d <= 2048, else 32 lanes x NW words, NW in {2,4,8}.
-__host__ __device__ inline uint32_t row_stride(uint32_t d) {
-  uint32_t w = (uint32_t)root_words(d);
-  if (w <= 32) return group_for_words(w);
-  uint32_t nw = (w + 31u) / 32u;
-  nw = nw <= 2 ? 2u : (nw <= 4 ? 4u : 8u);
-  return 32u * nw;
-}
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-__host__ __device__ inline size_t root_bytes(uint32_t d, bool pv, bool pa) {
-  size_t rs = row_stride(d);
-  size_t b = align16((size_t)d * 4);                 // list
-  b += align16((size_t)d * rs * 8);                  // rows
-  if (pv) b += align16((size_t)d * rs * 8);          // colT
-  if (pv) b += align16((size_t)d * 8);               // cnt
-  if (pa) b += align16((size_t)d * 8);               // per-arc sums
-  b += align16(((size_t)d + 1) * 4);                 // pair prefix
-  return b;
-}
-constexpr size_t kBlockMisc = 256;  // block scalars (counters, reduction slots)
-__host__ __device__ inline size_t light_slot_bytes(bool pv, bool pa) { return root_bytes(kLightMax, pv, pa); }
 
 // Process-wide count of kernel launches issued by this library.
 void note_launch(unsigned n = 1);
 
 // Launch helpers implemented in kc_count.cu / kc_orient.cu
-cudaError_t launch_count(const CountArgs &a, bool pv, bool pa, int grid, size_t smem, cudaStream_t s);
-int count_blocks_per_sm(bool pv, bool pa, size_t smem);
-cudaError_t set_count_smem(bool pv, bool pa, size_t smem);
+size_t block_root_smem(uint32_t dsmem, bool pv, bool pa, bool colT);
+uint32_t block_root_capacity(size_t smem_budget, bool pv, bool pa, bool colT);
+cudaError_t launch_count(const CountArgs &a, bool pv, bool pa, int block_grid, int warp_grid, size_t block_smem,
+                         cudaStream_t s);
+cudaError_t count_occupancy(bool pv, bool pa, size_t block_smem, int *block_per_sm, int *warp_per_sm);
 
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint64_t *out, size_t n, uint64_t *tmp, size_t tmp_elems,
                                cudaStream_t s);
