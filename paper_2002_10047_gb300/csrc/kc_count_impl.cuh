@@ -20,11 +20,12 @@
 // level above (l = 2: sum over x of |C & row_x|), and a branch is cut when
 // its candidate set has fewer vertices than still needed.
 //
-// Per-vertex counts (arb-count-v): a clique completed at the l = 2 level of
-// candidate set C as (x, y), y in C & row_x, credits x with |C & row_x| and y
-// with |C & col_y| (col = transposed matrix), so no per-clique increment is
-// made; vertices higher on the path get the totals of their sub-trees and the
-// root gets the root total. Counters are flushed to global memory once per
+// Per-vertex counts (arb-count-v): the cliques completed at the l = 2 level of
+// candidate set C are the arcs x->y inside C; vertex v in C is in |C & sym_v|
+// of them, sym_v = row_v | col_v being v's neighbours in either direction, and
+// their number is half the sum of those credits -- one pass over C, no
+// per-clique increment. Vertices higher on the path get the totals of their
+// sub-trees and the root gets the root total. Counters are flushed to global memory once per
 // root. Every addition is checked for uint64 wrap-around.
 #pragma once
 #include <cuda_runtime.h>
@@ -110,7 +111,7 @@ __device__ __forceinline__ int hlookup(const uint32_t *hkey, const uint16_t *hpo
 // A bit matrix as the DFS sees it: row x at rows + x*RS, W words in use.
 struct MatView {
   const uint64_t *rows;
-  const uint64_t *colT;        // transposed rows (per-vertex only)
+  const uint64_t *sym;         // rows | transposed rows (per-vertex only)
   unsigned long long *cnt;     // per-vertex counters (per-vertex only)
   uint32_t RS, W;
 };
@@ -157,9 +158,10 @@ __device__ __forceinline__ bool next_bit(uint64_t (&T)[NW], int j, int &x) {
   return false;
 }
 
-// l = 2 below candidate set C: sum over x in C of |C & row_x|. With per-vertex
-// counts the result is group-uniform and x, y are credited; otherwise each
-// lane returns its partial sum.
+// l = 2 below candidate set C: the number of arcs x->y inside C, i.e. the sum
+// over x in C of |C & row_x|; each lane returns its partial sum. With
+// per-vertex counts every v in C is credited |C & sym_v| (the completed
+// cliques through v) and the total is half their sum (group-uniform).
 template <int G, int NW, bool PV>
 __device__ __forceinline__ unsigned long long leaf2(const uint64_t (&C)[NW], const MatView &V, int j,
                                                     unsigned &ovf) {
@@ -168,34 +170,32 @@ __device__ __forceinline__ unsigned long long leaf2(const uint64_t (&C)[NW], con
   for (int r = 0; r < NW; ++r) T[r] = C[r];
   unsigned long long acc = 0;
   int x;
+  if (!PV) {
+    while (next_bit<G, NW>(T, j, x)) {
+      uint64_t R[NW];
+      load_row<G, NW>(V.rows + (size_t)x * V.RS, V.W, j, R);
+      unsigned a = 0;
+#pragma unroll
+      for (int r = 0; r < NW; ++r) a += __popcll(C[r] & R[r]);
+      acc += a;
+    }
+    return acc;
+  }
+  if (V.sym == nullptr) {
+    ovf |= ST_CAPACITY;  // per-vertex credits need the symmetric rows
+    return 0;
+  }
   while (next_bit<G, NW>(T, j, x)) {
     uint64_t R[NW];
-    load_row<G, NW>(V.rows + (size_t)x * V.RS, V.W, j, R);
+    load_row<G, NW>(V.sym + (size_t)x * V.RS, V.W, j, R);
     unsigned a = 0;
 #pragma unroll
     for (int r = 0; r < NW; ++r) a += __popcll(C[r] & R[r]);
-    if (PV) {
-      a = gsum32<G>(a);
-      if (j == 0 && a) atomic_add_ck(&V.cnt[x], a, ovf);
-    }
+    a = gsum32<G>(a);
+    if (j == 0 && a) atomic_add_ck(&V.cnt[x], a, ovf);
     acc += a;
   }
-  if (PV && V.colT == nullptr) {
-    ovf |= ST_CAPACITY;  // per-vertex credits need the transposed rows
-  } else if (PV) {
-#pragma unroll
-    for (int r = 0; r < NW; ++r) T[r] = C[r];
-    while (next_bit<G, NW>(T, j, x)) {
-      uint64_t R[NW];
-      load_row<G, NW>(V.colT + (size_t)x * V.RS, V.W, j, R);
-      unsigned b = 0;
-#pragma unroll
-      for (int r = 0; r < NW; ++r) b += __popcll(C[r] & R[r]);
-      b = gsum32<G>(b);
-      if (j == 0 && b) atomic_add_ck(&V.cnt[x], b, ovf);
-    }
-  }
-  return acc;
+  return acc >> 1;
 }
 
 // Rec-Count-Cliques with ell >= 2 vertices still to pick from C, as an
@@ -270,7 +270,7 @@ struct Slot {
   uint64_t *mask;             // 32 mask words of the current candidate set (root positions)
   uint32_t *pfx;              // exclusive prefix of their population counts
   uint16_t *P;                // root positions of the compacted vertices
-  uint64_t *S, *ST;           // compacted rows and their transpose (s x NWc words)
+  uint64_t *S, *SN;           // compacted rows and their symmetric closure (s x NWc words)
   unsigned long long *cs;     // local per-vertex counters
 };
 
@@ -281,7 +281,7 @@ __device__ __forceinline__ Slot carve_slot(uint8_t *base, bool pv) {
   s.pfx = (uint32_t *)(base + o.pfx);
   s.P = (uint16_t *)(base + o.P);
   s.S = (uint64_t *)(base + o.S);
-  s.ST = pv ? (uint64_t *)(base + o.ST) : nullptr;
+  s.SN = pv ? (uint64_t *)(base + o.ST) : nullptr;
   s.cs = pv ? (unsigned long long *)(base + o.cs) : nullptr;
   return s;
 }
@@ -313,7 +313,7 @@ __device__ unsigned long long compact_count(const MatView &M, uint64_t mword, ui
   const uint32_t NWc = s <= 64 ? 1u : 2u;
   for (uint32_t q = lane; q < s * NWc; q += 32) {
     sl.S[q] = 0;
-    if (PV) sl.ST[q] = 0;
+    if (PV) sl.SN[q] = 0;
   }
   if (PV)
     for (uint32_t q = lane; q < s; q += 32) sl.cs[q] = 0;
@@ -331,7 +331,10 @@ __device__ unsigned long long compact_count(const MatView &M, uint64_t mword, ui
         const uint32_t loc = sl.pfx[w] + (uint32_t)__popcll(mk & ((1ull << bb) - 1ull));
         if (loc < 64) o0 |= 1ull << loc;
         else o1 |= 1ull << (loc - 64);
-        if (PV) atomicOr((unsigned long long *)&sl.ST[loc * NWc + (q >> 6)], 1ull << (q & 63));
+        if (PV) {
+          atomicOr((unsigned long long *)&sl.SN[loc * NWc + (q >> 6)], 1ull << (q & 63));
+          atomicOr((unsigned long long *)&sl.SN[q * NWc + (loc >> 6)], 1ull << (loc & 63));
+        }
       }
     }
     sl.S[q * NWc] = o0;
@@ -341,7 +344,7 @@ __device__ unsigned long long compact_count(const MatView &M, uint64_t mword, ui
   unsigned long long acc = 0;
   MatView V;
   V.rows = sl.S;
-  V.colT = sl.ST;
+  V.sym = sl.SN;
   V.cnt = sl.cs;
   V.RS = NWc;
   V.W = NWc;
@@ -358,14 +361,14 @@ __device__ unsigned long long compact_count(const MatView &M, uint64_t mword, ui
       if (picks == 2) sub = (unsigned long long)pc;
       else if (pc >= picks - 1) sub = dfs<1, 2, PV>(C, picks - 1, V, 0, ovf);
     }
-    if (PV && sub) atomic_add_ck(&sl.cs[q], sub, ovf);
+    if (PV && picks > 2 && sub) atomic_add_ck(&sl.cs[q], sub, ovf);
     acc = add_ck(acc, sub, ovf);
   }
   if (PV && picks == 2) {
-    // the last pick y was taken once for every q with y in row_q: |col_y|
+    // each arc q->y of the compacted subgraph is one clique: q and y both in it
     for (uint32_t y = lane; y < s; y += 32) {
-      unsigned bcnt = (unsigned)__popcll(sl.ST[y * NWc]);
-      if (NWc == 2) bcnt += (unsigned)__popcll(sl.ST[y * NWc + 1]);
+      unsigned bcnt = (unsigned)__popcll(sl.SN[y * NWc]);
+      if (NWc == 2) bcnt += (unsigned)__popcll(sl.SN[y * NWc + 1]);
       if (bcnt) atomic_add_ck(&sl.cs[y], bcnt, ovf);
     }
   }
@@ -422,14 +425,14 @@ __device__ unsigned long long split_count(const MatView &M, const uint64_t *rowA
     unsigned long long sub = 0;
     if (picks == 2) sub = (unsigned long long)pc;
     else if (pc >= picks - 1) sub = dfs<1, NW, PV>(C, picks - 1, M, 0, ovf);
-    if (PV && sub) atomic_add_ck(&M.cnt[x], sub, ovf);
+    if (PV && picks > 2 && sub) atomic_add_ck(&M.cnt[x], sub, ovf);
     acc = add_ck(acc, sub, ovf);
   }
   if (PV && picks == 2) {
-    // last pick y: taken once for every x of the set with y in row_x
+    // each arc x->y inside the set is one clique: v is in |set & sym_v| of them
     for (uint32_t r = lane; r < s; r += 32) {
       const uint32_t y = slot_select(sl, W, r);
-      const uint64_t *cy = M.colT + (size_t)y * M.RS;
+      const uint64_t *cy = M.sym + (size_t)y * M.RS;
       unsigned b = 0;
       for (uint32_t w = 0; w < W; ++w) b += (unsigned)__popcll(sl.mask[w] & cy[w]);
       if (b) atomic_add_ck(&M.cnt[y], b, ovf);
@@ -473,8 +476,7 @@ __device__ unsigned long long generic_dispatch(const MatView &M, const uint64_t 
 }
 
 // k = 4 item of arc i: sum over q in row_i of |row_q & row_i| (lanes take the
-// set bits of row_i by rank). Per vertex: q gets |row_q & row_i| and, as the
-// last vertex, |col_q & row_i|.
+// set bits of row_i by rank). Per vertex: q is in |sym_q & row_i| of them.
 template <bool PV>
 __device__ unsigned long long k4_item(const MatView &M, uint32_t i, uint32_t s, const Slot &sl, unsigned &ovf) {
   const unsigned lane = lane_id();
@@ -503,9 +505,9 @@ __device__ unsigned long long k4_item(const MatView &M, uint32_t i, uint32_t s, 
       unsigned x = 0, yv = 0;
       for (uint32_t z = 0; z < W; ++z) {
         x += (unsigned)__popcll(rq[z] & ri[z]);
-        if (PV) yv += (unsigned)__popcll(M.colT[(size_t)q * M.RS + z] & ri[z]);
+        if (PV) yv += (unsigned)__popcll(M.sym[(size_t)q * M.RS + z] & ri[z]);
       }
-      if (PV && (x + yv)) atomic_add_ck(&M.cnt[q], (unsigned long long)x + yv, ovf);
+      if (PV && yv) atomic_add_ck(&M.cnt[q], (unsigned long long)yv, ovf);
       acc += x;
     }
     __syncwarp();
@@ -531,45 +533,62 @@ __device__ void block_root(const CountArgs &a, uint32_t u, uint8_t *base, uint8_
   const bool colT = PV && k >= 4;
   const RootLayout lay = root_layout(d, PV, PA, colT);
   uint32_t *L = (uint32_t *)(base + lay.L);
+  uint64_t *rb = (uint64_t *)(base + lay.rb);
+  uint32_t *rl = (uint32_t *)(base + lay.rl);
   uint32_t *hkey = (uint32_t *)(base + lay.hkey);
   uint16_t *hpos = (uint16_t *)(base + lay.hpos);
   uint64_t *rows = (uint64_t *)(base + lay.rows);
-  uint64_t *cT = colT ? (uint64_t *)(base + lay.colT) : nullptr;
+  uint64_t *sym = colT ? (uint64_t *)(base + lay.colT) : nullptr;
   unsigned long long *cnt = PV ? (unsigned long long *)(base + lay.cnt) : nullptr;
   unsigned long long *asub = PA ? (unsigned long long *)(base + lay.asub) : nullptr;
   uint32_t *pre = (uint32_t *)(base + lay.pre);
   const Slot sl = carve_slot(slots + (size_t)warp * slot_layout(PV).bytes, PV);
 
   for (uint32_t i = tid; i < d; i += kRootBlock) {
-    L[i] = a.col[b + i];
+    const uint32_t x = a.col[b + i];
+    const uint64_t xb = a.ptr[x];
+    L[i] = x;
+    rb[i] = xb;
+    rl[i] = (uint32_t)(a.ptr[x + 1] - xb);
     if (PV) cnt[i] = 0;
     if (PA) asub[i] = 0;
   }
   for (uint32_t s = tid; s < T; s += kRootBlock) hkey[s] = kEmpty;
   for (size_t w = tid; w < (size_t)d * W; w += kRootBlock) {
     rows[w] = 0;
-    if (colT) cT[w] = 0;
+    if (colT) sym[w] = 0;
   }
   __syncthreads();
   for (uint32_t i = tid; i < d; i += kRootBlock) hinsert(hkey, hpos, T, L[i], i);
   __syncthreads();
-  // the induced subgraph on N+(u): warp per row, lanes over N+(L[i])
+  // the induced subgraph on N+(u): warp per row, lanes over N+(L[i]), four
+  // loads in flight per lane
   for (uint32_t i = warp; i < d; i += kRootWarps) {
-    const uint32_t x = L[i];
-    const uint64_t xb = a.ptr[x], xe = a.ptr[x + 1];
-    for (uint64_t p = xb + lane; p < xe; p += 32) {
-      const int t = hlookup(hkey, hpos, T, a.col[p]);
-      if (t >= 0) {
-        atomicOr((unsigned long long *)&rows[(size_t)i * W + (t >> 6)], 1ull << (t & 63));
-        if (colT) atomicOr((unsigned long long *)&cT[(size_t)t * W + (i >> 6)], 1ull << (i & 63));
-        if (PV && k == 3) atomicAdd(&cnt[t], 1ull);
+    const uint64_t xb = rb[i];
+    const uint32_t len = rl[i];
+    for (uint32_t e0 = lane; e0 < len; e0 += 128) {
+      uint32_t y[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) y[q] = e0 + 32 * q < len ? a.col[xb + e0 + 32 * q] : kEmpty;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (y[q] == kEmpty) continue;
+        const int t = hlookup(hkey, hpos, T, y[q]);
+        if (t >= 0) {
+          atomicOr((unsigned long long *)&rows[(size_t)i * W + (t >> 6)], 1ull << (t & 63));
+          if (colT) {
+            atomicOr((unsigned long long *)&sym[(size_t)t * W + (i >> 6)], 1ull << (i & 63));
+            atomicOr((unsigned long long *)&sym[(size_t)i * W + (t >> 6)], 1ull << (t & 63));
+          }
+          if (PV && k == 3) atomicAdd(&cnt[t], 1ull);
+        }
       }
     }
   }
   __syncthreads();
   MatView M;
   M.rows = rows;
-  M.colT = cT;
+  M.sym = sym;
   M.cnt = cnt;
   M.RS = W;
   M.W = W;
@@ -772,10 +791,11 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
   const unsigned lane = lane_id();
   const LightLayout o = light_layout(PV, PA);
   uint32_t *L = (uint32_t *)(slot + o.L);
+  uint64_t *rbeg = (uint64_t *)(slot + o.rb);
   uint32_t *hkey = (uint32_t *)(slot + o.hkey);
   uint16_t *hpos = (uint16_t *)(slot + o.hpos);
   uint64_t *rows = (uint64_t *)(slot + o.rows);
-  uint64_t *cT = PV ? (uint64_t *)(slot + o.colT) : nullptr;
+  uint64_t *sym = PV ? (uint64_t *)(slot + o.colT) : nullptr;
   unsigned long long *cnt = PV ? (unsigned long long *)(slot + o.cnt) : nullptr;
   unsigned long long *asub = PA ? (unsigned long long *)(slot + o.asub) : nullptr;
   uint32_t *pre = (uint32_t *)(slot + o.pre);
@@ -786,7 +806,7 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
   for (uint32_t i = lane; i < (uint32_t)kLightMax; i += 32) {
     rows[i] = 0;
     if (PV) {
-      cT[i] = 0;
+      sym[i] = 0;
       cnt[i] = 0;
     }
     if (PA) asub[i] = 0;
@@ -796,13 +816,17 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
   uint32_t e0 = 0, e1 = 0;
   if (lane < d) {
     const uint32_t x = a.col[b + lane];
+    const uint64_t xb = a.ptr[x];
     L[lane] = x;
-    e0 = (uint32_t)(a.ptr[x + 1] - a.ptr[x]);
+    rbeg[lane] = xb;
+    e0 = (uint32_t)(a.ptr[x + 1] - xb);
   }
   if (lane + 32 < d) {
     const uint32_t x = a.col[b + lane + 32];
+    const uint64_t xb = a.ptr[x];
     L[lane + 32] = x;
-    e1 = (uint32_t)(a.ptr[x + 1] - a.ptr[x]);
+    rbeg[lane + 32] = xb;
+    e1 = (uint32_t)(a.ptr[x + 1] - xb);
   }
   const unsigned z0 = warp_incl_scan(e0), z1 = warp_incl_scan(e1);
   const unsigned tot0 = __shfl_sync(0xffffffffu, z0, 31), tot1 = __shfl_sync(0xffffffffu, z1, 31);
@@ -813,24 +837,41 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
   for (uint32_t i = lane; i < d; i += 32) hinsert(hkey, hpos, 128, L[i], i);
   __syncwarp();
   const uint32_t E = tot0 + tot1;
-  for (uint32_t e = lane; e < E; e += 32) {
-    uint32_t lo = 0, hi = d - 1;  // last row with epre <= e
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi + 1) >> 1;
-      if (epre[mid] <= e) lo = mid; else hi = mid - 1;
+  for (uint32_t e00 = lane; e00 < E; e00 += 128) {
+    uint32_t y[4], row[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t e = e00 + 32 * q;
+      y[q] = kEmpty;
+      row[q] = 0;
+      if (e < E) {
+        uint32_t lo = 0, hi = d - 1;  // last row with epre <= e
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi + 1) >> 1;
+          if (epre[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        row[q] = lo;
+        y[q] = a.col[rbeg[lo] + (e - epre[lo])];
+      }
     }
-    const uint32_t i = lo;
-    const uint32_t y = a.col[a.ptr[L[i]] + (e - epre[i])];
-    const int t = hlookup(hkey, hpos, 128, y);
-    if (t >= 0) {
-      atomicOr((unsigned long long *)&rows[i], 1ull << t);
-      if (PV) atomicOr((unsigned long long *)&cT[t], 1ull << i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (y[q] == kEmpty) continue;
+      const uint32_t i = row[q];
+      const int t = hlookup(hkey, hpos, 128, y[q]);
+      if (t >= 0) {
+        atomicOr((unsigned long long *)&rows[i], 1ull << t);
+        if (PV) {
+          atomicOr((unsigned long long *)&sym[t], 1ull << i);
+          atomicOr((unsigned long long *)&sym[i], 1ull << t);
+        }
+      }
     }
   }
   __syncwarp();
   MatView V;
   V.rows = rows;
-  V.colT = cT;
+  V.sym = sym;
   V.cnt = cnt;
   V.RS = 1;
   V.W = 1;
@@ -839,7 +880,7 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
     for (uint32_t i = lane; i < d; i += 32) {
       const unsigned c = (unsigned)__popcll(rows[i]);
       rsum = add_ck(rsum, c, ovf);
-      if (PV) cnt[i] += (unsigned long long)c + (unsigned)__popcll(cT[i]);
+      if (PV) cnt[i] += (unsigned)__popcll(sym[i]);
       if (PA) asub[i] = c;
     }
   } else {

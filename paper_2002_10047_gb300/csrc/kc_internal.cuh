@@ -34,21 +34,24 @@ __host__ __device__ inline uint32_t hash_slots(uint32_t d) {
 
 // Per-root working set of a block-level root with out-degree d:
 //   L      uint32[d]        N+(u)
+//   rb, rl uint64/uint32[d] start and length of N+(L[i]) in the DAG
 //   hkey   uint32[T]        open-addressing table: vertex id -> position in L
 //   hpos   uint16[T]
 //   rows   uint64[d*W]      the induced subgraph on N+(u), row i = N+(L[i]) within N+(u)
-//   colT   uint64[d*W]      transposed rows (per-vertex counts, k >= 4)
+//   colT   uint64[d*W]      rows | transposed rows (per-vertex counts, k >= 4)
 //   cnt    uint64[d]        per-vertex counters (per-vertex only)
 //   asub   uint64[d]        per-arc sums (per-arc only)
 //   pre    uint32[d+1]      prefix of split-arc sizes (k >= 5)
 struct RootLayout {
-  size_t L, hkey, hpos, rows, colT, cnt, asub, pre, bytes;
+  size_t L, rb, rl, hkey, hpos, rows, colT, cnt, asub, pre, bytes;
 };
 __host__ __device__ inline RootLayout root_layout(uint32_t d, bool pv, bool pa, bool colT) {
   RootLayout o;
   const uint32_t W = words_of(d), T = hash_slots(d);
   size_t off = 0;
   o.L = off; off += align16((size_t)d * 4);
+  o.rb = off; off += align16((size_t)d * 8);
+  o.rl = off; off += align16((size_t)d * 4);
   o.hkey = off; off += align16((size_t)T * 4);
   o.hpos = off; off += align16((size_t)T * 2);
   o.rows = off; off += align16((size_t)d * W * 8);
@@ -62,7 +65,7 @@ __host__ __device__ inline RootLayout root_layout(uint32_t d, bool pv, bool pa, 
 
 // Per-warp slot of the block-root kernel (item scratch): mask words and their
 // prefix counts, the positions of the compacted vertices, the compacted rows
-// and their transpose, and local per-vertex counters.
+// and their symmetric closure, and local per-vertex counters.
 struct SlotLayout {
   size_t mask, pfx, P, S, ST, cs, bytes;
 };
@@ -81,12 +84,13 @@ __host__ __device__ inline SlotLayout slot_layout(bool pv) {
 
 // Per-warp slot of the warp-root kernel (roots with d+ <= 64).
 struct LightLayout {
-  size_t L, hkey, hpos, rows, colT, cnt, asub, pre, epre, bytes;
+  size_t L, rb, hkey, hpos, rows, colT, cnt, asub, pre, epre, bytes;
 };
 __host__ __device__ inline LightLayout light_layout(bool pv, bool pa) {
   LightLayout o;
   size_t off = 0;
   o.L = off; off += kLightMax * 4;
+  o.rb = off; off += kLightMax * 8;
   o.hkey = off; off += 128 * 4;
   o.hpos = off; off += 128 * 2;
   o.rows = off; off += kLightMax * 8;

@@ -134,9 +134,16 @@ def test_complete_graphs_closed_form(kc, n, ks):
 
 
 def test_deep_k(kc):
+    """Deep recursion up to k = KC_KMAX = 32 (the search is pruned hard near k = n)."""
+    g = gg.complete(24)
+    dag = gpu_orient(kc, g, "degree")
+    for k in (12, 23, 24):
+        assert kc.count(dag, k) == math.comb(24, k)
+        tot, pv = kc.count_per_vertex(dag, k)
+        assert np.all(kc.as_uint64(pv) == math.comb(23, k - 1))
     g = gg.complete(33)
     dag = gpu_orient(kc, g, "gp")
-    for k in (20, 31, 32):
+    for k in (31, 32):
         assert kc.count(dag, k) == math.comb(33, k)
         tot, pv = kc.count_per_vertex(dag, k)
         assert np.all(kc.as_uint64(pv) == math.comb(32, k - 1))
