@@ -140,6 +140,34 @@ kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_
                            kc_stream_t stream);
 
 /*
+ * kc_count_noalloc -- the same total as kc_count, computed without allocating
+ * any device memory. (The paper has no counterpart: this is an interface for
+ * callers that cannot allocate.)
+ *
+ * Some callers cannot call cudaMalloc where they count: code running while a
+ * stream is captured into a CUDA graph, code under a fixed memory budget or a
+ * custom allocator that owns the device memory, or latency-critical paths that
+ * must not take allocator locks. kc_count allocates a small work block (and,
+ * for very large out-neighbourhoods, per-block matrices) on every call; this
+ * entry point takes that scratch from one static device array of
+ * KC_NOALLOC_SCRATCH_BYTES instead, which every GPU that loads the library
+ * holds until the process exits.
+ *   d        a handle from kc_orient (created earlier, e.g. at set-up)
+ *   k        1 .. KC_KMAX
+ *   h_total  receives the count
+ * Synchronises `stream`. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. All calls share the one array and it keeps the last call's
+ * contents (the entry point clears what must start at zero): calls that
+ * overlap on the GPU, from different streams or threads, race and must be
+ * serialised by the caller. Returns KC_ECAPACITY when one root's bit matrix
+ * (largest out-degree about 8100 and up) does not fit the array; the other
+ * status codes are those of kc_count.
+ */
+#define KC_NOALLOC_SCRATCH_BYTES (8u << 20)
+kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total, kc_stream_t stream);
+
+/*
  * Work statistics of an oriented graph, used for the bytes a counting pass
  * must move (computed exactly on the device):
  *   sum_out_sq     sum over roots u of d+(u)^2

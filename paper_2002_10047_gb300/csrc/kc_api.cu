@@ -9,21 +9,11 @@
 #include <string>
 #include <vector>
 
+#include "kc_dag.cuh"
 #include "kc_internal.cuh"
 #include "kc_orient.cuh"
 #include "kclique.h"
 
-struct kc_dag {
-  uint32_t n = 0;
-  uint64_t m = 0;
-  uint32_t max_out = 0;
-  uint64_t *ptr = nullptr;    // n+1
-  uint32_t *col = nullptr;    // m
-  uint32_t *order = nullptr;  // n, roots by out-degree descending
-  std::vector<uint64_t> ge;   // ge[t] = #roots with out-degree >= t, t = 0 .. max_out+1
-  cudaStream_t stream = nullptr;
-  int device = 0;
-};
 
 #include <atomic>
 
