@@ -74,7 +74,8 @@ typedef struct {
 
 /* Opaque oriented graph (the DAG DG of Algorithm 1) with library-owned device
  * buffers: out-lists N+(v) (neighbours later in the total order), each sorted
- * ascending, plus the root work list used by the counting kernels. */
+ * in the total order itself (by rank, the order that decided the arc
+ * directions), plus the root work list used by the counting kernels. */
 typedef struct kc_dag kc_dag;
 
 /*
@@ -101,7 +102,9 @@ uint32_t kc_dag_max_out_degree(const kc_dag *d);
 
 /*
  * Copy the oriented graph out (device to device): d_ptr uint64[n+1] and
- * d_col uint32[m], in the vertex ids of the input CSR. Either may be NULL.
+ * d_col uint32[m], in the vertex ids of the input CSR, each out-list in
+ * increasing rank (degree order: by (degree, id); Goodrich-Pszona: by
+ * (round, induced degree at removal, id)). Either may be NULL.
  * Synchronises `stream`.
  */
 kc_status kc_dag_export(const kc_dag *d, uint64_t *d_ptr, uint32_t *d_col, kc_stream_t stream);

@@ -69,6 +69,11 @@ int sm_count() {
 
 }  // namespace
 
+namespace kc {
+kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned long long *pa, uint64_t *h_total,
+                    uint64_t deadline_ns, cudaStream_t s);
+}  // namespace kc
+
 extern "C" {
 
 const char *kc_strerror(int status) {
@@ -187,6 +192,9 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   KC_CK(cudaMemcpyAsync(hist.p, start.data(), sizeof(unsigned) * start.size(), cudaMemcpyHostToDevice, s));
   KC_CK(cudaMallocAsync((void **)&D->order, sizeof(uint32_t) * n, s));
   KC_CK(kc::launch_outdeg_scatter(D->ptr, n, hist.as<unsigned>(), maxd, D->order, s));
+  // out-lists into the total order (positions inside N+(u) = ranks among N+(u))
+  auto ge = [&](uint64_t t) -> uint32_t { return t < D->ge.size() ? (uint32_t)D->ge[t] : 0u; };
+  KC_CK(kc::launch_sort_rows(D->ptr, D->col, key.as<uint64_t>(), D->order, ge(1025), ge(33), ge(2), maxd, s));
   KC_CK(cudaStreamSynchronize(s));  // `start` is a pageable host buffer read by the copy above
   *out = D;
   guard.d = nullptr;
@@ -206,15 +214,18 @@ kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t s
   if (!d || !h_stats) return KC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   DevBuf acc;
-  KC_CK(acc.alloc(sizeof(unsigned long long) * 3, s));
-  KC_CK(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 3, s));
+  KC_CK(acc.alloc(sizeof(unsigned long long) * 2, s));
+  KC_CK(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 2, s));
   if (d->n) KC_CK(kc::launch_dag_stats(d->ptr, d->col, d->n, acc.as<unsigned long long>(), s));
-  unsigned long long h[3];
+  unsigned long long h[2];
   KC_CK(cudaMemcpyAsync(h, acc.p, sizeof h, cudaMemcpyDeviceToHost, s));
   KC_CK(cudaStreamSynchronize(s));
+  uint64_t tri = 0;
+  const kc_status st = kc::run_count(d, 3, nullptr, nullptr, &tri, 0, s);
+  if (st != KC_OK) return st;
   h_stats->sum_out_sq = h[0];
   h_stats->sum_arc_head = h[1];
-  h_stats->triangles = h[2];
+  h_stats->triangles = tri;
   h_stats->max_out = d->max_out;
   return KC_OK;
 }
@@ -252,16 +263,15 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
   }
   if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
   const bool bpv = pv != nullptr, bpa = pa != nullptr;
-  const bool colT = bpv && k >= 4;
 
   // shared memory of a block root: per-warp item slots + the root's matrix
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t budget = (size_t)(optin > 4096 ? optin - 2048 : 48 * 1024);
-  const uint32_t dcap = block_root_capacity(budget, bpv, bpa, colT);
+  const uint32_t dcap = block_root_capacity(budget, bpv, bpa);
   const uint32_t dsmem = std::min<uint32_t>(dcap, std::max<uint32_t>(d->max_out, kLightMax + 1));
-  const size_t block_smem = block_root_smem(dsmem, bpv, bpa, colT);
+  const size_t block_smem = block_root_smem(dsmem, bpv, bpa);
   int per_sm_b = 0, per_sm_w = 0;
   KC_CK(count_occupancy(bpv, bpa, block_smem, &per_sm_b, &per_sm_w));
   const int sms = sm_count();
@@ -289,7 +299,7 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
   a.status = (unsigned *)(work.as<uint8_t>() + 8);
   a.queue = (unsigned *)(work.as<uint8_t>() + 16);
   if (a.n_scratch > 0) {
-    const size_t slab = (root_layout(d->max_out, bpv, bpa, colT).bytes + 255) & ~(size_t)255;
+    const size_t slab = (root_layout(d->max_out, bpv, bpa).bytes + 255) & ~(size_t)255;
     const size_t sbudget = (size_t)4 << 30;
     size_t nb = std::max<size_t>(1, sbudget / slab);
     nb = std::min<size_t>(nb, (size_t)block_grid);

@@ -20,13 +20,13 @@ extern template cudaError_t launch_variant<false, true>(const CountArgs &, int, 
 extern template cudaError_t launch_variant<true, false>(const CountArgs &, int, int, size_t, cudaStream_t);
 extern template cudaError_t launch_variant<true, true>(const CountArgs &, int, int, size_t, cudaStream_t);
 
-size_t block_root_smem(uint32_t dsmem, bool pv, bool pa, bool colT) {
-  return (size_t)kRootWarps * slot_layout(pv).bytes + (dsmem ? root_layout(dsmem, pv, pa, colT).bytes : 0);
+size_t block_root_smem(uint32_t dsmem, bool pv, bool pa) {
+  return (size_t)kRootWarps * slot_layout(pv).bytes + (dsmem ? root_layout(dsmem, pv, pa).bytes : 0);
 }
 
-uint32_t block_root_capacity(size_t smem_budget, bool pv, bool pa, bool colT) {
+uint32_t block_root_capacity(size_t smem_budget, bool pv, bool pa) {
   uint32_t d = kLightMax;
-  while (d < 4096 && block_root_smem(d + 1, pv, pa, colT) <= smem_budget) ++d;
+  while (d < 4096 && block_root_smem(d + 1, pv, pa) <= smem_budget) ++d;
   return d;
 }
 

@@ -6,26 +6,32 @@
 // root the team (one warp when d+(u) <= 64, one block otherwise) builds that
 // induced subgraph once -- "the induced subgraph on N_DG(v)" of Section 3.3 --
 // as a bit matrix over positions 0..d-1 in N+(u) (the relabelling to
-// [0, O(alpha)] of Section 3.3): row i holds N+(N+(u)[i]) within N+(u).
-// Membership of an out-neighbour in N+(u) is found through an open-addressing
-// hash table in shared memory.
+// [0, O(alpha)] of Section 3.3). Out-lists are sorted by rank, so position
+// order is rank order: an arc between positions i < t points from i to t. One
+// matrix (adj) holds the subgraph: its upper triangle (bit t of row i, t > i)
+// is the arc set; per-vertex counting also fills the mirrored lower triangle,
+// so that row v holds all of v's neighbours. Membership of an out-neighbour in
+// N+(u) is found through a shared-memory hash table.
 //
-// Below the root the work is split by arcs (edge parallelism, Section 3.3):
-// the candidates of arc u->x_i are row_i = N+(u) ∩ N+(x_i). For k >= 5 a warp
-// compacts that intersection (or, when it has more than 128 vertices, the
-// intersection with one more vertex) to local ids 0..s-1: its own bit matrix
-// of s <= 128 rows of one or two words. The warp's lanes then split the first
-// level of that matrix and run Rec-Count-Cliques in registers: intersect =
-// word-wise AND, |I| = population count, the base case l = 1 folded into the
-// level above (l = 2: sum over x of |C & row_x|), and a branch is cut when
-// its candidate set has fewer vertices than still needed.
+// Rec-Count-Cliques (Algorithm 1) runs on bitsets: the candidates are visited
+// in increasing position, and when x is taken the candidates still left are
+// exactly those ranked after x, so "intersect I with N+(x)" is the remaining
+// candidates AND adj[x]; |I| is a population count; the base case l = 1 is
+// folded into the level above (l = 2: the number of arcs inside the candidate
+// set); a branch is cut when it has fewer candidates than vertices still
+// needed.
 //
-// Per-vertex counts (arb-count-v): the cliques completed at the l = 2 level of
-// candidate set C are the arcs x->y inside C; vertex v in C is in |C & sym_v|
-// of them, sym_v = row_v | col_v being v's neighbours in either direction, and
-// their number is half the sum of those credits -- one pass over C, no
-// per-clique increment. Vertices higher on the path get the totals of their
-// sub-trees and the root gets the root total. Counters are flushed to global memory once per
+// Work split below the root (edge parallelism, Section 3.3): one warp item per
+// arc u->x_i (k <= 5, and k >= 6 when the arc has at most 128 candidates) or
+// per triangle u->x_i->x_a (k >= 6 when the arc has more). For k >= 6 the
+// item's candidate set is compacted to local ids 0..s-1 (s <= 128, one or two
+// words per row) and the warp's lanes split its first level, each running the
+// recursion in registers.
+//
+// Per-vertex counts (arb-count-v): the cliques completed at an l = 2 level of
+// candidate set C are the arcs inside C; vertex v in C lies on |C & adj[v]| of
+// them. Vertices higher on the path get the totals of their sub-trees and the
+// root gets the root total. Counters are flushed to global memory once per
 // root. Every addition is checked for uint64 wrap-around.
 #pragma once
 #include <cuda_runtime.h>
@@ -76,6 +82,15 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {
   return v;
 }
 
+// bits strictly above position x, restricted to word w
+__device__ __forceinline__ uint64_t above_word(uint32_t x, uint32_t w) {
+  const uint32_t xw = x >> 6;
+  if (w < xw) return 0ull;
+  if (w > xw) return ~0ull;
+  const uint32_t b = x & 63u;
+  return b == 63u ? 0ull : (~0ull << (b + 1u));
+}
+
 // ------------------------------------------------------------ hash table
 constexpr uint32_t kEmpty = 0xffffffffu;
 
@@ -107,12 +122,54 @@ __device__ __forceinline__ int hlookup(const uint32_t *hkey, const uint16_t *hpo
   return -1;
 }
 
+// Set bit t of row r (stride W words) for every lane with `hit`, one shared
+// atomic per distinct (row, word) of the warp: lanes walking one row would
+// otherwise serialise on the same words. Called by all 32 lanes.
+__device__ __forceinline__ void warp_set_bits(uint64_t *adj, uint32_t W, bool hit, uint32_t r, uint32_t t) {
+  const unsigned lane = lane_id();
+  const uint32_t key = r * 256u + (t >> 6);
+  unsigned todo = __ballot_sync(0xffffffffu, hit);
+  while (todo) {
+    const int ld = __ffs(todo) - 1;
+    const uint32_t kl = __shfl_sync(0xffffffffu, key, ld);
+    const bool mine = hit && key == kl;
+    const uint64_t b = mine ? (1ull << (t & 63)) : 0ull;
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)b);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(b >> 32));
+    if (lane == (unsigned)ld)
+      atomicOr((unsigned long long *)&adj[(size_t)r * W + (t >> 6)], ((unsigned long long)hi << 32) | lo);
+    todo &= ~__ballot_sync(0xffffffffu, mine);
+  }
+}
+
+// Packed table (id << 16 | position), one 64-bit load per probe (block roots).
+constexpr unsigned long long kEmptySlot = ~0ull;
+
+__device__ __forceinline__ void pinsert(unsigned long long *tab, uint32_t T, uint32_t y, uint32_t pos) {
+  uint32_t s = hslot(y, T - 1);
+  const unsigned long long v = ((unsigned long long)y << 16) | pos;
+  for (uint32_t probe = 0; probe < T; ++probe) {
+    if (atomicCAS(&tab[s], kEmptySlot, v) == kEmptySlot) return;
+    s = (s + 1) & (T - 1);
+  }
+}
+
+__device__ __forceinline__ int plookup(const unsigned long long *tab, uint32_t T, uint32_t y) {
+  uint32_t s = hslot(y, T - 1);
+  for (uint32_t probe = 0; probe < T; ++probe) {
+    const unsigned long long v = tab[s];
+    if (v == kEmptySlot) return -1;
+    if ((uint32_t)(v >> 16) == y) return (int)(v & 0xffffu);
+    s = (s + 1) & (T - 1);
+  }
+  return -1;
+}
+
 // ---------------------------------------------------------- DFS engine
-// A bit matrix as the DFS sees it: row x at rows + x*RS, W words in use.
+// A symmetric bit matrix as the DFS sees it: row x at adj + x*RS, W words in use.
 struct MatView {
-  const uint64_t *rows;
-  const uint64_t *sym;         // rows | transposed rows (per-vertex only)
-  unsigned long long *cnt;     // per-vertex counters (per-vertex only)
+  const uint64_t *adj;
+  unsigned long long *cnt;  // per-vertex counters (per-vertex only)
   uint32_t RS, W;
 };
 
@@ -123,17 +180,18 @@ __device__ __forceinline__ unsigned gsum32(unsigned v) {
 }
 
 // Lane j of a G-lane group (G = 1 or 32) holds words r*G + j (r < NW) of a
-// set; words at or past W read as zero (a one-word set always has W = 1).
+// set; words at or past W read as zero.
 template <int G, int NW>
 __device__ __forceinline__ void load_row(const uint64_t *base, uint32_t W, int j, uint64_t (&out)[NW]) {
 #pragma unroll
   for (int r = 0; r < NW; ++r) {
     const uint32_t w = (uint32_t)(r * G + j);
-    out[r] = (NW == 1 || w < W) ? base[w] : 0ull;
+    out[r] = (NW == 1 && G == 1) ? base[0] : (w < W ? base[w] : 0ull);
   }
 }
 
-// Next set bit of a group-distributed set; clears it and returns its position.
+// Next set bit of a group-distributed set (ascending); clears it, so T then
+// holds exactly the members after x.
 template <int G, int NW>
 __device__ __forceinline__ bool next_bit(uint64_t (&T)[NW], int j, int &x) {
 #pragma unroll
@@ -158,51 +216,166 @@ __device__ __forceinline__ bool next_bit(uint64_t (&T)[NW], int j, int &x) {
   return false;
 }
 
-// l = 2 below candidate set C: the number of arcs x->y inside C, i.e. the sum
-// over x in C of |C & row_x|; each lane returns its partial sum. With
-// per-vertex counts every v in C is credited |C & sym_v| (the completed
-// cliques through v) and the total is half their sum (group-uniform).
+// l = 2 below candidate set C: the number of arcs inside C (lane partials).
+// Per vertex: every v in C is credited |C & adj[v]| and the (group-uniform)
+// total is half their sum.
+//
+// One lane (G = 1): the members are walked word by word (the word loop is
+// unrolled, so every word index is static); while word r is walked, the
+// candidates still left have no bits below word r, so the AND/POPC of the
+// count skips those words.
 template <int G, int NW, bool PV>
-__device__ __forceinline__ unsigned long long leaf2(const uint64_t (&C)[NW], const MatView &V, int j,
-                                                    unsigned &ovf) {
-  uint64_t T[NW];
-#pragma unroll
-  for (int r = 0; r < NW; ++r) T[r] = C[r];
+__device__ __forceinline__ unsigned long long leaf2(const uint64_t (&C)[NW], const MatView V, int j,
+                                                    unsigned &ovf_out) {
+  unsigned ovf = 0;
   unsigned long long acc = 0;
-  int x;
-  if (!PV) {
-    while (next_bit<G, NW>(T, j, x)) {
-      uint64_t R[NW];
-      load_row<G, NW>(V.rows + (size_t)x * V.RS, V.W, j, R);
-      unsigned a = 0;
+  if constexpr (G == 1 && NW <= 2) {
 #pragma unroll
-      for (int r = 0; r < NW; ++r) a += __popcll(C[r] & R[r]);
+    for (int r = 0; r < NW; ++r) {
+      uint64_t t = C[r];
+      while (t) {
+        const int x = r * 64 + __ffsll((long long)t) - 1;
+        t &= t - 1;
+        const uint64_t *row = V.adj + (size_t)x * V.RS;
+        unsigned a = 0;
+        if (PV) {
+#pragma unroll
+          for (int q = 0; q < NW; ++q) a += __popcll(C[q] & row[q]);
+          if (a) atomic_add_ck(&V.cnt[x], a, ovf);
+        } else {
+          a = __popcll(t & row[r]);
+#pragma unroll
+          for (int q = r + 1; q < NW; ++q) a += __popcll(C[q] & row[q]);
+        }
+        acc += a;
+      }
+    }
+  } else if constexpr (G == 1) {
+    // wide sets: one loop body, the next member found branch-free; the count
+    // reads only the words at or above the member's word
+    uint64_t T[NW];
+#pragma unroll
+    for (int r = 0; r < NW; ++r) T[r] = C[r];
+    for (;;) {
+      int x = -1;
+#pragma unroll
+      for (int r = 0; r < NW; ++r) {
+        if (x < 0 && T[r]) {
+          x = r * 64 + __ffsll((long long)T[r]) - 1;
+          T[r] &= T[r] - 1;
+        }
+      }
+      if (x < 0) break;
+      const uint64_t *row = V.adj + (size_t)x * V.RS;
+      const int rx = x >> 6;
+      unsigned a = 0;
+      if (PV) {
+#pragma unroll
+        for (int q = 0; q < NW; ++q) a += __popcll(C[q] & row[q]);
+        if (a) atomic_add_ck(&V.cnt[x], a, ovf);
+      } else {
+#pragma unroll
+        for (int q = 0; q < NW; ++q)
+          if (q >= rx) a += __popcll(T[q] & row[q]);
+      }
       acc += a;
     }
-    return acc;
-  }
-  if (V.sym == nullptr) {
-    ovf |= ST_CAPACITY;  // per-vertex credits need the symmetric rows
-    return 0;
-  }
-  while (next_bit<G, NW>(T, j, x)) {
-    uint64_t R[NW];
-    load_row<G, NW>(V.sym + (size_t)x * V.RS, V.W, j, R);
-    unsigned a = 0;
+  } else {
+    uint64_t T[NW];
 #pragma unroll
-    for (int r = 0; r < NW; ++r) a += __popcll(C[r] & R[r]);
-    a = gsum32<G>(a);
-    if (j == 0 && a) atomic_add_ck(&V.cnt[x], a, ovf);
-    acc += a;
+    for (int r = 0; r < NW; ++r) T[r] = C[r];
+    int x;
+    while (next_bit<G, NW>(T, j, x)) {
+      uint64_t R[NW];
+      load_row<G, NW>(V.adj + (size_t)x * V.RS, V.W, j, R);
+      unsigned a = 0;
+      if (PV) {
+#pragma unroll
+        for (int r = 0; r < NW; ++r) a += __popcll(C[r] & R[r]);
+        a = gsum32<G>(a);
+        if (j == 0 && a) atomic_add_ck(&V.cnt[x], a, ovf);
+      } else {
+#pragma unroll
+        for (int r = 0; r < NW; ++r) a += __popcll(T[r] & R[r]);
+      }
+      acc += a;
+    }
   }
-  return acc >> 1;
+  ovf_out |= ovf;
+  return PV ? (acc >> 1) : acc;
 }
 
-// Rec-Count-Cliques with ell >= 2 vertices still to pick from C, as an
-// explicit stack; returns lane partials (group-uniform with per-vertex).
+// Rec-Count-Cliques with L >= 3 vertices still to pick from C, L fixed at
+// compile time so the levels stay in registers.
+template <int G, int NW, bool PV, int L>
+__device__ __forceinline__ unsigned long long dfs_fixed(const uint64_t (&C)[NW], const MatView V, int j,
+                                                        unsigned &ovf_out) {
+  if constexpr (L == 2) {
+    return leaf2<G, NW, PV>(C, V, j, ovf_out);
+  } else {
+    unsigned ovf = 0;
+    unsigned long long sum = 0;
+    if constexpr (G == 1) {
+      // one loop body (no per-word copies of the deeper levels): the next
+      // member is found branch-free with static word indices
+      uint64_t T[NW];
+#pragma unroll
+      for (int r = 0; r < NW; ++r) T[r] = C[r];
+      for (;;) {
+        int x = -1;
+#pragma unroll
+        for (int r = 0; r < NW; ++r) {
+          if (x < 0 && T[r]) {
+            x = r * 64 + __ffsll((long long)T[r]) - 1;
+            T[r] &= T[r] - 1;
+          }
+        }
+        if (x < 0) break;
+        const uint64_t *row = V.adj + (size_t)x * V.RS;
+        uint64_t Cn[NW];
+        unsigned c = 0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) {
+          Cn[q] = T[q] & row[q];
+          c += __popcll(Cn[q]);
+        }
+        if ((int)c < L - 1) continue;
+        const unsigned long long sub = dfs_fixed<G, NW, PV, L - 1>(Cn, V, j, ovf);
+        sum = add_ck(sum, sub, ovf);
+        if (PV) atomic_add_ck(&V.cnt[x], sub, ovf);
+      }
+    } else {
+      uint64_t T[NW];
+#pragma unroll
+      for (int r = 0; r < NW; ++r) T[r] = C[r];
+      int x;
+      while (next_bit<G, NW>(T, j, x)) {
+        uint64_t R[NW], Cn[NW];
+        load_row<G, NW>(V.adj + (size_t)x * V.RS, V.W, j, R);
+        unsigned c = 0;
+#pragma unroll
+        for (int r = 0; r < NW; ++r) {
+          Cn[r] = T[r] & R[r];
+          c += __popcll(Cn[r]);
+        }
+        c = gsum32<G>(c);
+        if ((int)c < L - 1) continue;
+        const unsigned long long sub = dfs_fixed<G, NW, PV, L - 1>(Cn, V, j, ovf);
+        sum = add_ck(sum, sub, ovf);
+        if (PV && j == 0) atomic_add_ck(&V.cnt[x], sub, ovf);
+      }
+    }
+    ovf_out |= ovf;
+    return sum;
+  }
+}
+
+constexpr int kFixedMax = 6;  // deeper recursions use the explicit stack
+
+// Rec-Count-Cliques for any ell >= 2 with an explicit stack (ell > kFixedMax).
 template <int G, int NW, bool PV>
-__device__ unsigned long long dfs(const uint64_t (&C0)[NW], int ell, const MatView &V, int j, unsigned &ovf) {
-  if (ell == 2) return leaf2<G, NW, PV>(C0, V, j, ovf);
+__device__ unsigned long long dfs_stack(const uint64_t (&C0)[NW], int ell, const MatView V, int j, unsigned &ovf_out) {
+  unsigned ovf = 0;
   uint64_t Cs[kMaxFrames][NW], Ts[kMaxFrames][NW];
   unsigned long long subs[kMaxFrames];
   int xs[kMaxFrames];
@@ -215,10 +388,10 @@ __device__ unsigned long long dfs(const uint64_t (&C0)[NW], int ell, const MatVi
     const int l = ell - top;
     unsigned long long a = 0;
     bool done = false;
-    uint64_t C[NW];
-#pragma unroll
-    for (int r = 0; r < NW; ++r) C[r] = Cs[top][r];
     if (l == 2) {
+      uint64_t C[NW];
+#pragma unroll
+      for (int r = 0; r < NW; ++r) C[r] = Cs[top][r];
       a = leaf2<G, NW, PV>(C, V, j, ovf);
       done = true;
     } else {
@@ -234,11 +407,11 @@ __device__ unsigned long long dfs(const uint64_t (&C0)[NW], int ell, const MatVi
         done = true;
       } else {
         uint64_t R[NW], Cn[NW];
-        load_row<G, NW>(V.rows + (size_t)x * V.RS, V.W, j, R);
+        load_row<G, NW>(V.adj + (size_t)x * V.RS, V.W, j, R);
         unsigned c = 0;
 #pragma unroll
         for (int r = 0; r < NW; ++r) {
-          Cn[r] = C[r] & R[r];
+          Cn[r] = T[r] & R[r];
           c += __popcll(Cn[r]);
         }
         c = gsum32<G>(c);
@@ -262,16 +435,39 @@ __device__ unsigned long long dfs(const uint64_t (&C0)[NW], int ell, const MatVi
       if (PV && j == 0) atomic_add_ck(&V.cnt[xs[top]], a, ovf);
     }
   }
-  return ret;
+  { const auto ret_ = (ret); ovf_out |= ovf; return ret_; }
+}
+
+// ell >= 2 vertices still to pick from C. Register-resident levels are used
+// while their sets stay small (two words: six levels, four words: four
+// levels, wider: the leaf only); deeper recursions use the explicit stack.
+template <int G, int NW, bool PV>
+__device__ __forceinline__ unsigned long long dfs(const uint64_t (&C)[NW], int ell, const MatView V, int j,
+                                                  unsigned &ovf) {
+  constexpr int kFix = (G == 1 && NW <= 2) ? kFixedMax : ((G == 1 && NW <= 4) ? 4 : 2);
+  if (ell == 2) return leaf2<G, NW, PV>(C, V, j, ovf);
+  if constexpr (kFix >= 3) {
+    if (ell == 3) return dfs_fixed<G, NW, PV, 3>(C, V, j, ovf);
+  }
+  if constexpr (kFix >= 4) {
+    if (ell == 4) return dfs_fixed<G, NW, PV, 4>(C, V, j, ovf);
+  }
+  if constexpr (kFix >= 5) {
+    if (ell == 5) return dfs_fixed<G, NW, PV, 5>(C, V, j, ovf);
+  }
+  if constexpr (kFix >= 6) {
+    if (ell == 6) return dfs_fixed<G, NW, PV, 6>(C, V, j, ovf);
+  }
+  return dfs_stack<G, NW, PV>(C, ell, V, j, ovf);
 }
 
 // ----------------------------------------------------- warp item engines
 struct Slot {
-  uint64_t *mask;             // 32 mask words of the current candidate set (root positions)
-  uint32_t *pfx;              // exclusive prefix of their population counts
-  uint16_t *P;                // root positions of the compacted vertices
-  uint64_t *S, *SN;           // compacted rows and their symmetric closure (s x NWc words)
-  unsigned long long *cs;     // local per-vertex counters
+  uint64_t *mask;          // up to 32 mask words of the current candidate set (root positions)
+  uint32_t *pfx;           // exclusive prefix of their population counts (33 entries)
+  uint16_t *P;             // root positions of the compacted vertices
+  uint64_t *S;             // compacted symmetric rows (s x NWc words)
+  unsigned long long *cs;  // local per-vertex counters
 };
 
 __device__ __forceinline__ Slot carve_slot(uint8_t *base, bool pv) {
@@ -281,108 +477,28 @@ __device__ __forceinline__ Slot carve_slot(uint8_t *base, bool pv) {
   s.pfx = (uint32_t *)(base + o.pfx);
   s.P = (uint16_t *)(base + o.P);
   s.S = (uint64_t *)(base + o.S);
-  s.SN = pv ? (uint64_t *)(base + o.ST) : nullptr;
   s.cs = pv ? (unsigned long long *)(base + o.cs) : nullptr;
   return s;
 }
 
-// Count the cliques that take `picks` (>= 2) more vertices from a candidate set
-// of s <= kCompactMax root positions whose words (W <= 32) lane w holds in
-// mword. The set is compacted to local ids 0..s-1, its induced rows are
-// extracted from the root matrix, and the lanes split the first pick.
-// Per-vertex credits of the picked vertices go to the root counters rc.
-// Returns the warp-uniform total.
-template <bool PV>
-__device__ unsigned long long compact_count(const MatView &M, uint64_t mword, uint32_t s, int picks, const Slot &sl,
-                                            unsigned long long *rc, unsigned &ovf) {
+// Lane w (< W <= 32) holds word w of a candidate set over root positions:
+// store the words and their prefix counts in the slot; returns |set|.
+__device__ __forceinline__ uint32_t slot_set(const Slot sl, uint64_t mword, uint32_t W) {
   const unsigned lane = lane_id();
-  const uint32_t W = M.W;
   const unsigned c = lane < W ? (unsigned)__popcll(mword) : 0u;
-  const unsigned pfx = warp_incl_scan(c) - c;
+  const unsigned incl = warp_incl_scan(c);
   if (lane < W) {
     sl.mask[lane] = mword;
-    sl.pfx[lane] = pfx;
-    uint64_t bw = mword;
-    unsigned r = pfx;
-    while (bw) {
-      if (r < (unsigned)kCompactMax) sl.P[r] = (uint16_t)(lane * 64 + __ffsll((long long)bw) - 1);
-      ++r;
-      bw &= bw - 1;
-    }
+    sl.pfx[lane] = incl - c;
   }
-  const uint32_t NWc = s <= 64 ? 1u : 2u;
-  for (uint32_t q = lane; q < s * NWc; q += 32) {
-    sl.S[q] = 0;
-    if (PV) sl.SN[q] = 0;
-  }
-  if (PV)
-    for (uint32_t q = lane; q < s; q += 32) sl.cs[q] = 0;
+  const uint32_t s = __shfl_sync(0xffffffffu, incl, 31);
+  if (lane == 0) sl.pfx[W] = s;
   __syncwarp();
-  // bit b of compacted row q <=> P[b] in N+(P[q]) within the set
-  for (uint32_t q = lane; q < s; q += 32) {
-    const uint64_t *src = M.rows + (size_t)sl.P[q] * M.RS;
-    uint64_t o0 = 0, o1 = 0;
-    for (uint32_t w = 0; w < W; ++w) {
-      const uint64_t mk = sl.mask[w];
-      uint64_t bits = src[w] & mk;
-      while (bits) {
-        const int bb = __ffsll((long long)bits) - 1;
-        bits &= bits - 1;
-        const uint32_t loc = sl.pfx[w] + (uint32_t)__popcll(mk & ((1ull << bb) - 1ull));
-        if (loc < 64) o0 |= 1ull << loc;
-        else o1 |= 1ull << (loc - 64);
-        if (PV) {
-          atomicOr((unsigned long long *)&sl.SN[loc * NWc + (q >> 6)], 1ull << (q & 63));
-          atomicOr((unsigned long long *)&sl.SN[q * NWc + (loc >> 6)], 1ull << (loc & 63));
-        }
-      }
-    }
-    sl.S[q * NWc] = o0;
-    if (NWc == 2) sl.S[q * NWc + 1] = o1;
-  }
-  __syncwarp();
-  unsigned long long acc = 0;
-  MatView V;
-  V.rows = sl.S;
-  V.sym = sl.SN;
-  V.cnt = sl.cs;
-  V.RS = NWc;
-  V.W = NWc;
-  for (uint32_t q = lane; q < s; q += 32) {
-    unsigned long long sub = 0;
-    if (NWc == 1) {
-      uint64_t C[1] = {sl.S[q]};
-      const int pc = __popcll(C[0]);
-      if (picks == 2) sub = (unsigned long long)pc;
-      else if (pc >= picks - 1) sub = dfs<1, 1, PV>(C, picks - 1, V, 0, ovf);
-    } else {
-      uint64_t C[2] = {sl.S[2 * q], sl.S[2 * q + 1]};
-      const int pc = __popcll(C[0]) + __popcll(C[1]);
-      if (picks == 2) sub = (unsigned long long)pc;
-      else if (pc >= picks - 1) sub = dfs<1, 2, PV>(C, picks - 1, V, 0, ovf);
-    }
-    if (PV && picks > 2 && sub) atomic_add_ck(&sl.cs[q], sub, ovf);
-    acc = add_ck(acc, sub, ovf);
-  }
-  if (PV && picks == 2) {
-    // each arc q->y of the compacted subgraph is one clique: q and y both in it
-    for (uint32_t y = lane; y < s; y += 32) {
-      unsigned bcnt = (unsigned)__popcll(sl.SN[y * NWc]);
-      if (NWc == 2) bcnt += (unsigned)__popcll(sl.SN[y * NWc + 1]);
-      if (bcnt) atomic_add_ck(&sl.cs[y], bcnt, ovf);
-    }
-  }
-  __syncwarp();
-  if (PV)
-    for (uint32_t q = lane; q < s; q += 32) atomic_add_ck(&rc[sl.P[q]], sl.cs[q], ovf);
-  const unsigned long long tot = warp_sum64_ck(acc, ovf);
-  __syncwarp();
-  return tot;
+  return s;
 }
 
-// Position of the r-th set bit of the set whose words and exclusive prefix
-// counts are in the slot (W <= 32 words).
-__device__ __forceinline__ uint32_t slot_select(const Slot &sl, uint32_t W, uint32_t r) {
+// position of the r-th member of the slot's set
+__device__ __forceinline__ uint32_t slot_select(const Slot sl, uint32_t W, uint32_t r) {
   uint32_t lo = 0, hi = W - 1;  // last word with pfx <= r
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;
@@ -393,33 +509,104 @@ __device__ __forceinline__ uint32_t slot_select(const Slot &sl, uint32_t W, uint
   return lo * 64 + (uint32_t)(__ffsll((long long)bb) - 1);
 }
 
-// Lanes split the first pick of the candidate set rowA & rowB (root
-// positions, W <= NW <= 32 words) and each lane runs the DFS on the root's
-// rows with NW-word sets in registers. Per-vertex credits go to the root
-// counters of M. Returns the warp-uniform total.
-template <int NW, bool PV>
-__device__ unsigned long long split_count(const MatView &M, const uint64_t *rowA, const uint64_t *rowB, int picks,
-                                          const Slot &sl, unsigned &ovf) {
+// Cliques taking `picks` (>= 2) more vertices from the slot's set of
+// s <= kCompactMax root positions: the set is compacted to local ids 0..s-1
+// (rank order is kept), its induced symmetric rows are extracted from the
+// root matrix, and the lanes split the first pick. Per-vertex credits of the
+// picked vertices go to the root counters rc. Returns the warp-uniform total.
+template <bool PV>
+__device__ unsigned long long compact_count(const MatView M, uint32_t s, int picks, const Slot sl,
+                                            unsigned long long *rc, unsigned &ovf_out) {
+  unsigned ovf = 0;
   const unsigned lane = lane_id();
   const uint32_t W = M.W;
-  const uint64_t mw = lane < W ? (rowA[lane] & (rowB ? rowB[lane] : ~0ull)) : 0ull;
-  const unsigned c = (unsigned)__popcll(mw);
-  const unsigned incl = warp_incl_scan(c);
-  const uint32_t s = __shfl_sync(0xffffffffu, incl, 31);
   if (lane < W) {
-    sl.mask[lane] = mw;
-    sl.pfx[lane] = incl - c;
+    uint64_t bw = sl.mask[lane];
+    unsigned r = sl.pfx[lane];
+    while (bw) {
+      if (r < (unsigned)kCompactMax) sl.P[r] = (uint16_t)(lane * 64 + __ffsll((long long)bw) - 1);
+      ++r;
+      bw &= bw - 1;
+    }
+  }
+  if (PV)
+    for (uint32_t q = lane; q < s; q += 32) sl.cs[q] = 0;
+  __syncwarp();
+  const uint32_t NWc = s <= 64 ? 1u : 2u;
+  // bit b of compacted row q <=> P[b] adjacent to P[q]
+  for (uint32_t q = lane; q < s; q += 32) {
+    const uint64_t *src = M.adj + (size_t)sl.P[q] * M.RS;
+    uint64_t o0 = 0, o1 = 0;
+    for (uint32_t w = 0; w < W; ++w) {
+      const uint64_t mk = sl.mask[w];
+      uint64_t bits = src[w] & mk;
+      while (bits) {
+        const int bb = __ffsll((long long)bits) - 1;
+        bits &= bits - 1;
+        const uint32_t loc = sl.pfx[w] + (uint32_t)__popcll(mk & ((1ull << bb) - 1ull));
+        if (loc < 64) o0 |= 1ull << loc;
+        else o1 |= 1ull << (loc - 64);
+      }
+    }
+    sl.S[q * NWc] = o0;
+    if (NWc == 2) sl.S[q * NWc + 1] = o1;
   }
   __syncwarp();
   unsigned long long acc = 0;
+  MatView V;
+  V.adj = sl.S;
+  V.cnt = sl.cs;
+  V.RS = NWc;
+  V.W = NWc;
+  for (uint32_t q = lane; q < s; q += 32) {
+    unsigned long long sub = 0;
+    if (NWc == 1) {
+      uint64_t C[1] = {sl.S[q] & above_word(q, 0)};
+      const int pc = __popcll(C[0]);
+      if (picks == 2) sub = (unsigned long long)pc;
+      else if (pc >= picks - 1) sub = dfs<1, 1, PV>(C, picks - 1, V, 0, ovf);
+    } else {
+      uint64_t C[2] = {sl.S[2 * q] & above_word(q, 0), sl.S[2 * q + 1] & above_word(q, 1)};
+      const int pc = __popcll(C[0]) + __popcll(C[1]);
+      if (picks == 2) sub = (unsigned long long)pc;
+      else if (pc >= picks - 1) sub = dfs<1, 2, PV>(C, picks - 1, V, 0, ovf);
+    }
+    if (PV && picks > 2 && sub) atomic_add_ck(&sl.cs[q], sub, ovf);
+    acc = add_ck(acc, sub, ovf);
+  }
+  if (PV && picks == 2) {
+    // each arc of the compacted subgraph is one clique: q lies on all its arcs
+    for (uint32_t q = lane; q < s; q += 32) {
+      unsigned b = (unsigned)__popcll(sl.S[q * NWc]);
+      if (NWc == 2) b += (unsigned)__popcll(sl.S[q * NWc + 1]);
+      if (b) atomic_add_ck(&sl.cs[q], b, ovf);
+    }
+  }
+  __syncwarp();
+  if (PV)
+    for (uint32_t q = lane; q < s; q += 32) atomic_add_ck(&rc[sl.P[q]], sl.cs[q], ovf);
+  const unsigned long long tot = warp_sum64_ck(acc, ovf);
+  __syncwarp();
+  { const auto ret_ = (tot); ovf_out |= ovf; return ret_; }
+}
+
+// Lanes split the first pick of the slot's set (root positions, W <= NW <= 32
+// words) and each lane runs the recursion on the root matrix with NW-word sets
+// in registers. Returns the warp-uniform total.
+template <int NW, bool PV>
+__device__ unsigned long long split_count(const MatView M, uint32_t s, int picks, const Slot sl, unsigned &ovf_out) {
+  unsigned ovf = 0;
+  const unsigned lane = lane_id();
+  const uint32_t W = M.W;
+  unsigned long long acc = 0;
   for (uint32_t r = lane; r < s; r += 32) {
     const uint32_t x = slot_select(sl, W, r);
-    const uint64_t *rx = M.rows + (size_t)x * M.RS;
+    const uint64_t *rx = M.adj + (size_t)x * M.RS;
     uint64_t C[NW];
     int pc = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
-      C[w] = (uint32_t)w < W ? (sl.mask[w] & rx[w]) : 0ull;
+      C[w] = (uint32_t)w < W ? (sl.mask[w] & rx[w] & above_word(x, (uint32_t)w)) : 0ull;
       pc += __popcll(C[w]);
     }
     unsigned long long sub = 0;
@@ -429,91 +616,95 @@ __device__ unsigned long long split_count(const MatView &M, const uint64_t *rowA
     acc = add_ck(acc, sub, ovf);
   }
   if (PV && picks == 2) {
-    // each arc x->y inside the set is one clique: v is in |set & sym_v| of them
+    // each arc inside the set is one clique: v lies on |set & adj[v]| of them
     for (uint32_t r = lane; r < s; r += 32) {
       const uint32_t y = slot_select(sl, W, r);
-      const uint64_t *cy = M.sym + (size_t)y * M.RS;
+      const uint64_t *cy = M.adj + (size_t)y * M.RS;
       unsigned b = 0;
       for (uint32_t w = 0; w < W; ++w) b += (unsigned)__popcll(sl.mask[w] & cy[w]);
       if (b) atomic_add_ck(&M.cnt[y], b, ovf);
     }
   }
   __syncwarp();
-  return warp_sum64_ck(acc, ovf);
+  { const auto ret_ = (warp_sum64_ck(acc, ovf)); ovf_out |= ovf; return ret_; }
 }
 
-// Lanes-over-words engine for a candidate set too large to compact: the warp
-// is one 32-lane group, lane j holding words r*32 + j of the root's rows.
+// Lanes-over-words engine for roots wider than 32 words (d+ > 2048): the warp
+// is one 32-lane group, lane j holding words r*32 + j of set & rowB.
 template <int NW, bool PV>
-__device__ unsigned long long generic_count(const MatView &M, const uint64_t *rowA, const uint64_t *rowB, int picks,
-                                            unsigned &ovf) {
+__device__ unsigned long long generic_count(const MatView M, const uint64_t *rowA, uint32_t xa, const uint64_t *rowB,
+                                            uint32_t xb, int picks, unsigned &ovf_out) {
+  unsigned ovf = 0;
   const int j = (int)lane_id();
   uint64_t C[NW];
 #pragma unroll
   for (int r = 0; r < NW; ++r) {
     const uint32_t w = (uint32_t)(r * 32 + j);
-    C[r] = w < M.W ? (rowA[w] & (rowB ? rowB[w] : ~0ull)) : 0ull;
+    uint64_t v = 0;
+    if (w < M.W) {
+      v = rowA[w] & above_word(xa, w);
+      if (rowB) v &= rowB[w] & above_word(xb, w);
+    }
+    C[r] = v;
   }
   unsigned long long s = dfs<32, NW, PV>(C, picks, M, j, ovf);
   if (!PV) s = warp_sum64_ck(s, ovf);
-  return s;
+  { const auto ret_ = (s); ovf_out |= ovf; return ret_; }
 }
 
 template <bool PV>
-__device__ unsigned long long generic_dispatch(const MatView &M, const uint64_t *rowA, const uint64_t *rowB,
-                                               int picks, const Slot &sl, unsigned &ovf, unsigned *status) {
-  if (M.W <= 2) return split_count<2, PV>(M, rowA, rowB, picks, sl, ovf);
-  if (M.W <= 4) return split_count<4, PV>(M, rowA, rowB, picks, sl, ovf);
-  if (M.W <= 8) return split_count<8, PV>(M, rowA, rowB, picks, sl, ovf);
-  if (M.W <= 12) return split_count<12, PV>(M, rowA, rowB, picks, sl, ovf);
+__device__ unsigned long long generic_dispatch(const MatView M, const uint64_t *rowA, uint32_t xa,
+                                               const uint64_t *rowB, uint32_t xb, int picks, unsigned &ovf,
+                                               unsigned *status) {
   const uint32_t nw = (M.W + 31u) / 32u;
-  if (nw <= 1) return generic_count<1, PV>(M, rowA, rowB, picks, ovf);
-  if (nw <= 2) return generic_count<2, PV>(M, rowA, rowB, picks, ovf);
-  if (nw <= 4) return generic_count<4, PV>(M, rowA, rowB, picks, ovf);
-  if (nw <= 8) return generic_count<8, PV>(M, rowA, rowB, picks, ovf);
+  if (nw <= 2) return generic_count<2, PV>(M, rowA, xa, rowB, xb, picks, ovf);
+  if (nw <= 4) return generic_count<4, PV>(M, rowA, xa, rowB, xb, picks, ovf);
+  if (nw <= 8) return generic_count<8, PV>(M, rowA, xa, rowB, xb, picks, ovf);
   if (lane_id() == 0) atomicOr(status, ST_CAPACITY);
   return 0;
 }
 
-// k = 4 item of arc i: sum over q in row_i of |row_q & row_i| (lanes take the
-// set bits of row_i by rank). Per vertex: q is in |sym_q & row_i| of them.
+// Lanes-over-words for a set already in the slot (W <= 32 words).
 template <bool PV>
-__device__ unsigned long long k4_item(const MatView &M, uint32_t i, uint32_t s, const Slot &sl, unsigned &ovf) {
+__device__ unsigned long long wide_count(const MatView M, int picks, const Slot sl, unsigned &ovf_out) {
+  unsigned ovf = 0;
+  const int j = (int)lane_id();
+  uint64_t C[1] = {(uint32_t)j < M.W ? sl.mask[j] : 0ull};
+  unsigned long long s = dfs<32, 1, PV>(C, picks, M, j, ovf);
+  if (!PV) s = warp_sum64_ck(s, ovf);
+  { const auto ret_ = (s); ovf_out |= ovf; return ret_; }
+}
+
+template <bool PV>
+__device__ unsigned long long split_dispatch(const MatView M, uint32_t s, int picks, const Slot sl, unsigned &ovf) {
+  if (M.W <= 2) return split_count<2, PV>(M, s, picks, sl, ovf);
+  if (M.W <= 4) return split_count<4, PV>(M, s, picks, sl, ovf);
+  if (M.W <= 8) return split_count<8, PV>(M, s, picks, sl, ovf);
+  if (M.W <= 12) return split_count<12, PV>(M, s, picks, sl, ovf);
+  return wide_count<PV>(M, picks, sl, ovf);
+}
+
+// k = 4 item of arc i (set = out-neighbours of x_i within N+(u), in the slot):
+// the arcs inside the set; per vertex q lies on |set & adj[q]| of them.
+template <bool PV>
+__device__ unsigned long long k4_item(const MatView M, uint32_t s, const Slot sl, unsigned &ovf_out) {
+  unsigned ovf = 0;
   const unsigned lane = lane_id();
   const uint32_t W = M.W;
-  const uint64_t *ri = M.rows + (size_t)i * M.RS;
   unsigned long long acc = 0;
-  for (uint32_t w0 = 0; w0 < W; w0 += 32) {
-    // chunks of 32 words (W > 32 only for roots in global scratch)
-    const uint32_t wn = min(32u, W - w0);
-    const uint64_t mword = lane < wn ? ri[w0 + lane] : 0ull;
-    const unsigned c = (unsigned)__popcll(mword);
-    const unsigned incl = warp_incl_scan(c);
-    const unsigned cs = __shfl_sync(0xffffffffu, incl, 31);
-    if (lane < wn) {
-      sl.mask[lane] = mword;
-      sl.pfx[lane] = incl - c;
+  for (uint32_t r = lane; r < s; r += 32) {
+    const uint32_t q = slot_select(sl, W, r);
+    const uint64_t *rq = M.adj + (size_t)q * M.RS;
+    unsigned x = 0, yv = 0;
+    for (uint32_t z = 0; z < W; ++z) {
+      const uint64_t m = sl.mask[z] & rq[z];
+      x += (unsigned)__popcll(m & above_word(q, z));
+      if (PV) yv += (unsigned)__popcll(m);
     }
-    __syncwarp();
-    for (uint32_t r = lane; r < cs; r += 32) {
-      uint32_t w = 0;
-      while (w + 1 < wn && sl.pfx[w + 1] <= r) ++w;
-      uint64_t bb = sl.mask[w];
-      for (uint32_t q = r - sl.pfx[w]; q; --q) bb &= bb - 1;
-      const uint32_t q = (w0 + w) * 64 + (uint32_t)(__ffsll((long long)bb) - 1);
-      const uint64_t *rq = M.rows + (size_t)q * M.RS;
-      unsigned x = 0, yv = 0;
-      for (uint32_t z = 0; z < W; ++z) {
-        x += (unsigned)__popcll(rq[z] & ri[z]);
-        if (PV) yv += (unsigned)__popcll(M.sym[(size_t)q * M.RS + z] & ri[z]);
-      }
-      if (PV && yv) atomic_add_ck(&M.cnt[q], (unsigned long long)yv, ovf);
-      acc += x;
-    }
-    __syncwarp();
+    if (PV && yv) atomic_add_ck(&M.cnt[q], yv, ovf);
+    acc += x;
   }
-  (void)s;
-  return warp_sum64_ck(acc, ovf);
+  { const auto ret_ = (warp_sum64_ck(acc, ovf)); ovf_out |= ovf; return ret_; }
 }
 
 // ------------------------------------------------------- block-level root
@@ -522,28 +713,46 @@ struct BlockShared {
   unsigned root, next, items, pad;
 };
 
+// block-wide exclusive scan of one value per thread (kRootBlock threads)
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned long long *red, unsigned *total) {
+  const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+  const unsigned incl = warp_incl_scan(v);
+  if (lane == 31) red[warp] = incl;
+  __syncthreads();
+  unsigned off = 0, all = 0;
+  for (int w = 0; w < kRootWarps; ++w) {
+    if (w < (int)warp) off += (unsigned)red[w];
+    all += (unsigned)red[w];
+  }
+  __syncthreads();
+  *total = all;
+  return off + incl - v;
+}
+
 template <bool PV, bool PA>
-__device__ void block_root(const CountArgs &a, uint32_t u, uint8_t *base, uint8_t *slots, unsigned long long &tsum,
-                           unsigned &ovf, BlockShared &sh) {
+__device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8_t *base, uint8_t *slots, unsigned long long &tsum_out,
+                           unsigned &ovf_out, BlockShared &sh) {
+  unsigned ovf = 0;
+  unsigned long long tsum = 0;
   const unsigned tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   const uint64_t b = a.ptr[u];
   const uint32_t d = (uint32_t)(a.ptr[u + 1] - b);
   const uint32_t W = words_of(d), T = hash_slots(d);
   const int k = a.k;
-  const bool colT = PV && k >= 4;
-  const RootLayout lay = root_layout(d, PV, PA, colT);
+  const RootLayout lay = root_layout(d, PV, PA);
   uint32_t *L = (uint32_t *)(base + lay.L);
   uint64_t *rb = (uint64_t *)(base + lay.rb);
   uint32_t *rl = (uint32_t *)(base + lay.rl);
-  uint32_t *hkey = (uint32_t *)(base + lay.hkey);
-  uint16_t *hpos = (uint16_t *)(base + lay.hpos);
-  uint64_t *rows = (uint64_t *)(base + lay.rows);
-  uint64_t *sym = colT ? (uint64_t *)(base + lay.colT) : nullptr;
+  unsigned long long *tab = (unsigned long long *)(base + lay.hslot);
+  uint64_t *adj = (uint64_t *)(base + lay.adj);
   unsigned long long *cnt = PV ? (unsigned long long *)(base + lay.cnt) : nullptr;
   unsigned long long *asub = PA ? (unsigned long long *)(base + lay.asub) : nullptr;
   uint32_t *pre = (uint32_t *)(base + lay.pre);
   const Slot sl = carve_slot(slots + (size_t)warp * slot_layout(PV).bytes, PV);
 
+  // N+(u) and the extents of its members' out-lists
+  const uint32_t per = (d + kRootBlock - 1) / kRootBlock;
+  const uint32_t c0 = min(d, tid * per), c1 = min(d, c0 + per);
   for (uint32_t i = tid; i < d; i += kRootBlock) {
     const uint32_t x = a.col[b + i];
     const uint64_t xb = a.ptr[x];
@@ -553,83 +762,91 @@ __device__ void block_root(const CountArgs &a, uint32_t u, uint8_t *base, uint8_
     if (PV) cnt[i] = 0;
     if (PA) asub[i] = 0;
   }
-  for (uint32_t s = tid; s < T; s += kRootBlock) hkey[s] = kEmpty;
-  for (size_t w = tid; w < (size_t)d * W; w += kRootBlock) {
-    rows[w] = 0;
-    if (colT) sym[w] = 0;
-  }
+  for (uint32_t s = tid; s < T; s += kRootBlock) tab[s] = kEmptySlot;
+  for (size_t w = tid; w < (size_t)d * W; w += kRootBlock) adj[w] = 0;
+  if (tid == 0) sh.next = 0;
   __syncthreads();
-  for (uint32_t i = tid; i < d; i += kRootBlock) hinsert(hkey, hpos, T, L[i], i);
+  for (uint32_t i = tid; i < d; i += kRootBlock) pinsert(tab, T, L[i], i);
   __syncthreads();
-  // the induced subgraph on N+(u): warp per row, lanes over N+(L[i]), four
-  // loads in flight per lane
-  for (uint32_t i = warp; i < d; i += kRootWarps) {
+  // the induced subgraph on N+(u): warps take whole rows (row i = N+(L[i]));
+  // eight loads in flight per lane. Out-lists are in rank order, so the hits
+  // of one row arrive in increasing position and the row's bits are set with
+  // one atomic per distinct word.
+  for (;;) {
+    unsigned i = 0;
+    if (lane == 0) i = atomicAdd(&sh.next, 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= d) break;
     const uint64_t xb = rb[i];
     const uint32_t len = rl[i];
-    for (uint32_t e0 = lane; e0 < len; e0 += 128) {
-      uint32_t y[4];
+    constexpr int U = 8;
+    for (uint32_t base = 0; base < len; base += 32 * U) {
+      uint32_t y[U];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) y[q] = e0 + 32 * q < len ? a.col[xb + e0 + 32 * q] : kEmpty;
+      for (int q = 0; q < U; ++q) {
+        const uint32_t e = base + lane + 32 * q;
+        y[q] = e < len ? a.col[xb + e] : kEmpty;
+      }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (y[q] == kEmpty) continue;
-        const int t = hlookup(hkey, hpos, T, y[q]);
-        if (t >= 0) {
-          atomicOr((unsigned long long *)&rows[(size_t)i * W + (t >> 6)], 1ull << (t & 63));
-          if (colT) {
-            atomicOr((unsigned long long *)&sym[(size_t)t * W + (i >> 6)], 1ull << (i & 63));
-            atomicOr((unsigned long long *)&sym[(size_t)i * W + (t >> 6)], 1ull << (t & 63));
-          }
-          if (PV && k == 3) atomicAdd(&cnt[t], 1ull);
+      for (int q = 0; q < U; ++q) {
+        const int t = y[q] == kEmpty ? -1 : plookup(tab, T, y[q]);
+        const bool hit = t >= 0;
+        const uint32_t w = hit ? ((uint32_t)t >> 6) : 0u;
+        unsigned todo = __ballot_sync(0xffffffffu, hit);
+        while (todo) {
+          const int ld = __ffs(todo) - 1;
+          const uint32_t wl = __shfl_sync(0xffffffffu, w, ld);
+          const bool mine = hit && w == wl;
+          const uint64_t bit = mine ? (1ull << (t & 63)) : 0ull;
+          const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)bit);
+          const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(bit >> 32));
+          if (lane == (unsigned)ld)
+            atomicOr((unsigned long long *)&adj[(size_t)i * W + wl], ((unsigned long long)hi << 32) | lo);
+          todo &= ~__ballot_sync(0xffffffffu, mine);
         }
+        // the lower triangle is read only by the per-vertex credits
+        if (PV && hit) atomicOr((unsigned long long *)&adj[(size_t)t * W + (i >> 6)], 1ull << (i & 63));
       }
     }
   }
   __syncthreads();
   MatView M;
-  M.rows = rows;
-  M.sym = sym;
+  M.adj = adj;
   M.cnt = cnt;
   M.RS = W;
   M.W = W;
   unsigned long long rsum = 0;  // lane 0 of each warp holds its item totals
   if (k == 3) {
     for (uint32_t i = tid; i < d; i += kRootBlock) {
-      unsigned c = 0;
-      for (uint32_t w = 0; w < W; ++w) c += (unsigned)__popcll(rows[(size_t)i * W + w]);
+      unsigned c = 0, call = 0;
+      for (uint32_t w = 0; w < W; ++w) {
+        const uint64_t v = adj[(size_t)i * W + w];
+        c += (unsigned)__popcll(v & above_word(i, w));
+        if (PV) call += (unsigned)__popcll(v);
+      }
       rsum = add_ck(rsum, c, ovf);
-      if (PV) cnt[i] += c;  // cnt[i] already holds i's in-degree within N+(u)
+      if (PV) cnt[i] = call;  // triangles u-i-t for every neighbour t of i in N+(u)
       if (PA) asub[i] = c;
     }
   } else {
     const bool compactable = W <= (uint32_t)kCompactWords;
     uint32_t nitems = d;
-    if (k >= 5) {
-      // arcs whose candidate sets are too big to compact are split by their
-      // next vertex; pre[] numbers those pair items
-      const uint32_t per = (d + kRootBlock - 1) / kRootBlock;
-      const uint32_t c0 = min(d, tid * per), c1 = min(d, c0 + per);
-      unsigned loc = 0;
+    if (k >= 6 && compactable) {
+      // arcs with more than kCompactMax candidates are split by their next vertex
+      unsigned cl = 0;
       for (uint32_t i = c0; i < c1; ++i) {
         unsigned c = 0;
-        for (uint32_t w = 0; w < W; ++w) c += (unsigned)__popcll(rows[(size_t)i * W + w]);
-        c = (k >= 6 && compactable && c > (unsigned)kCompactMax) ? c : 0u;
+        for (uint32_t w = 0; w < W; ++w) c += (unsigned)__popcll(adj[(size_t)i * W + w] & above_word(i, w));
+        c = c > (unsigned)kCompactMax ? c : 0u;
         pre[i] = c;
-        loc += c;
+        cl += c;
       }
-      const unsigned incl = warp_incl_scan(loc);
-      if (lane == 31) sh.red[warp] = incl;
-      __syncthreads();
-      unsigned off = 0, all = 0;
-      for (int w = 0; w < kRootWarps; ++w) {
-        if (w < (int)warp) off += (unsigned)sh.red[w];
-        all += (unsigned)sh.red[w];
-      }
-      off += incl - loc;
+      unsigned all;
+      unsigned o2 = block_excl_scan(cl, sh.red, &all);
       for (uint32_t i = c0; i < c1; ++i) {
         const uint32_t c = pre[i];
-        pre[i] = off;
-        off += c;
+        pre[i] = o2;
+        o2 += c;
       }
       if (tid == 0) {
         pre[d] = all;
@@ -648,34 +865,40 @@ __device__ void block_root(const CountArgs &a, uint32_t u, uint8_t *base, uint8_
       unsigned long long item = 0;
       uint32_t i, av = 0xffffffffu;
       if (t < d) {
+        // arc item: candidates = out-neighbours of x_i inside N+(u)
         i = t;
-        const uint64_t *ri = rows + (size_t)i * W;
-        unsigned s = 0;
-        for (uint32_t w = lane; w < W; w += 32) s += (unsigned)__popcll(ri[w]);
-        s = __reduce_add_sync(0xffffffffu, s);
-        if (k == 4) {
-          if (s >= 2) item = k4_item<PV>(M, i, s, sl, ovf);
-        } else if (s >= (unsigned)(k - 2)) {
-          if (k == 5 || !compactable) {
-            item = generic_dispatch<PV>(M, ri, nullptr, k - 2, sl, ovf, a.status);
-          } else if (s <= (unsigned)kCompactMax) {
-            item = compact_count<PV>(M, lane < W ? ri[lane] : 0ull, s, k - 2, sl, cnt, ovf);
-          }  // else: split into pair items below
+        const uint64_t *ri = adj + (size_t)i * W;
+        if (!compactable) {
+          unsigned s = 0;
+          for (uint32_t w = lane; w < W; w += 32) s += (unsigned)__popcll(ri[w] & above_word(i, w));
+          s = __reduce_add_sync(0xffffffffu, s);
+          if (s >= (unsigned)(k - 2)) item = generic_dispatch<PV>(M, ri, i, nullptr, 0, k - 2, ovf, a.status);
+        } else {
+          const uint32_t s = slot_set(sl, lane < W ? (ri[lane] & above_word(i, lane)) : 0ull, W);
+          if (s >= (uint32_t)(k - 2)) {
+            if (k == 4) {
+              item = k4_item<PV>(M, s, sl, ovf);
+            } else if (k == 5 && (W <= 2 || s > (uint32_t)kCompactMax)) {
+              item = split_dispatch<PV>(M, s, 3, sl, ovf);  // one level below: compaction does not pay
+            } else if (s <= (uint32_t)kCompactMax) {
+              item = compact_count<PV>(M, s, k - 2, sl, cnt, ovf);
+            }  // else (k >= 6): split into pair items
+          }
         }
       } else {
-        // pair item: arc i (more than kCompactMax candidates) and its r-th candidate av
+        // pair item: arc i and its r-th candidate av
         const uint32_t tt = t - d;
         uint32_t lo = 0, hi = d;  // last i with pre[i] <= tt
         while (lo < hi) {
           const uint32_t mid = (lo + hi + 1) >> 1;
           if (pre[mid] <= tt) lo = mid; else hi = mid - 1;
         }
-        i = lo;
-        const uint64_t *ri = rows + (size_t)min(i, d - 1) * W;
-        const uint64_t wv = (lane < W && i < d) ? ri[lane] : 0ull;
+        i = lo < d ? lo : d - 1;
+        const uint64_t *ri = adj + (size_t)i * W;
+        const uint64_t wv = lane < W ? (ri[lane] & above_word(i, lane)) : 0ull;
         const unsigned c = (unsigned)__popcll(wv);
         const unsigned incl = warp_incl_scan(c);
-        const unsigned r = i < d ? tt - pre[i] : 0xffffffffu;
+        const unsigned r = tt - pre[i];
         const unsigned hit = __ballot_sync(0xffffffffu, lane < W && r < incl && r >= incl - c);
         if (hit) {
           const int wl = __ffs(hit) - 1;
@@ -685,15 +908,16 @@ __device__ void block_root(const CountArgs &a, uint32_t u, uint8_t *base, uint8_
             av = lane * 64 + (uint32_t)(__ffsll((long long)bb) - 1);
           }
           av = __shfl_sync(0xffffffffu, av, wl);
-          const uint64_t *rv = rows + (size_t)av * W;
-          const uint64_t mw = lane < W ? (ri[lane] & rv[lane]) : 0ull;
-          const unsigned s0 = __reduce_add_sync(0xffffffffu, (unsigned)__popcll(mw));
-          if (s0 >= (unsigned)(k - 3)) {
-            if (s0 <= (unsigned)kCompactMax) item = compact_count<PV>(M, mw, s0, k - 3, sl, cnt, ovf);
-            else item = generic_dispatch<PV>(M, ri, rv, k - 3, sl, ovf, a.status);
+          const uint64_t *rv = adj + (size_t)av * W;
+          const uint64_t mw = lane < W ? (wv & rv[lane] & above_word(av, lane)) : 0ull;
+          const uint32_t s0 = slot_set(sl, mw, W);
+          if (s0 >= (uint32_t)(k - 3)) {
+            if (s0 <= (uint32_t)kCompactMax) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf);
+            else item = split_dispatch<PV>(M, s0, k - 3, sl, ovf);
           }
-        } else if (lane == 0) {
-          atomicOr(a.status, ST_CAPACITY);
+        } else {
+          if (lane == 0) atomicOr(a.status, ST_CAPACITY);
+          av = 0xffffffffu;
         }
       }
       if (lane == 0 && item) {
@@ -722,6 +946,8 @@ __device__ void block_root(const CountArgs &a, uint32_t u, uint8_t *base, uint8_
     for (uint32_t i = tid; i < d; i += kRootBlock) a.pa[b + i] = asub[i];
   tsum = add_ck(tsum, rsum, ovf);
   __syncthreads();
+  ovf_out |= ovf;
+  tsum_out = add_ck(tsum_out, tsum, ovf_out);
 }
 
 __device__ __forceinline__ bool past_deadline(const CountArgs &a) {
@@ -733,7 +959,7 @@ __device__ __forceinline__ bool past_deadline(const CountArgs &a) {
 }
 
 __device__ inline void finish_block(const CountArgs &a, unsigned long long tsum, unsigned ovf, unsigned long long *red,
-                             int nwarps) {
+                                    int nwarps) {
   const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
   __syncthreads();
   const unsigned long long r = warp_sum64_ck(tsum, ovf);
@@ -752,7 +978,7 @@ __device__ inline void finish_block(const CountArgs &a, unsigned long long tsum,
 // scratch (largest out-degrees), then the shared-memory ones, all in order of
 // decreasing out-degree.
 template <bool PV, bool PA>
-__global__ void __launch_bounds__(kRootBlock) count_block_kernel(CountArgs a) {
+__global__ void __launch_bounds__(kRootBlock, 1) count_block_kernel(CountArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ BlockShared sh;
   const unsigned tid = threadIdx.x;
@@ -786,16 +1012,17 @@ __global__ void __launch_bounds__(kRootBlock) count_block_kernel(CountArgs a) {
 // Roots with d+ <= 64: one warp, rows of one word, items over lanes (arcs for
 // k = 4, triangles u->x_i->x_j for k >= 5, each lane one item).
 template <bool PV, bool PA>
-__device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigned long long &tsum, unsigned &ovf,
+__device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigned long long &tsum_out, unsigned &ovf_out,
                           unsigned *w_next) {
+  unsigned ovf = 0;
+  unsigned long long tsum = 0;
   const unsigned lane = lane_id();
   const LightLayout o = light_layout(PV, PA);
   uint32_t *L = (uint32_t *)(slot + o.L);
   uint64_t *rbeg = (uint64_t *)(slot + o.rb);
   uint32_t *hkey = (uint32_t *)(slot + o.hkey);
   uint16_t *hpos = (uint16_t *)(slot + o.hpos);
-  uint64_t *rows = (uint64_t *)(slot + o.rows);
-  uint64_t *sym = PV ? (uint64_t *)(slot + o.colT) : nullptr;
+  uint64_t *adj = (uint64_t *)(slot + o.adj);
   unsigned long long *cnt = PV ? (unsigned long long *)(slot + o.cnt) : nullptr;
   unsigned long long *asub = PA ? (unsigned long long *)(slot + o.asub) : nullptr;
   uint32_t *pre = (uint32_t *)(slot + o.pre);
@@ -804,15 +1031,11 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
   const uint32_t d = (uint32_t)(a.ptr[u + 1] - b);
   const int k = a.k;
   for (uint32_t i = lane; i < (uint32_t)kLightMax; i += 32) {
-    rows[i] = 0;
-    if (PV) {
-      sym[i] = 0;
-      cnt[i] = 0;
-    }
+    adj[i] = 0;
+    if (PV) cnt[i] = 0;
     if (PA) asub[i] = 0;
   }
   for (uint32_t s = lane; s < 128; s += 32) hkey[s] = kEmpty;
-  // flattened adjacency of the rows: element e of the concatenation of N+(L[i])
   uint32_t e0 = 0, e1 = 0;
   if (lane < d) {
     const uint32_t x = a.col[b + lane];
@@ -836,58 +1059,53 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
   __syncwarp();
   for (uint32_t i = lane; i < d; i += 32) hinsert(hkey, hpos, 128, L[i], i);
   __syncwarp();
+  // the concatenated rows, eight loads in flight per lane; rows past d are empty
   const uint32_t E = tot0 + tot1;
-  for (uint32_t e00 = lane; e00 < E; e00 += 128) {
-    uint32_t y[4], row[4];
+  {
+    constexpr int U = 8;
+    uint32_t i = 0;
+    for (uint32_t base = 0; base < E; base += 32 * U) {  // warp-uniform trip count
+      uint32_t y[U], row[U];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t e = e00 + 32 * q;
-      y[q] = kEmpty;
-      row[q] = 0;
-      if (e < E) {
-        uint32_t lo = 0, hi = d - 1;  // last row with epre <= e
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi + 1) >> 1;
-          if (epre[mid] <= e) lo = mid; else hi = mid - 1;
+      for (int q = 0; q < U; ++q) {
+        const uint32_t e = base + lane + 32 * q;
+        y[q] = kEmpty;
+        row[q] = 0;
+        if (e < E) {
+          while (epre[i + 1] <= e) ++i;
+          row[q] = i;
+          y[q] = a.col[rbeg[i] + (e - epre[i])];
         }
-        row[q] = lo;
-        y[q] = a.col[rbeg[lo] + (e - epre[lo])];
       }
-    }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (y[q] == kEmpty) continue;
-      const uint32_t i = row[q];
-      const int t = hlookup(hkey, hpos, 128, y[q]);
-      if (t >= 0) {
-        atomicOr((unsigned long long *)&rows[i], 1ull << t);
-        if (PV) {
-          atomicOr((unsigned long long *)&sym[t], 1ull << i);
-          atomicOr((unsigned long long *)&sym[i], 1ull << t);
-        }
+      for (int q = 0; q < U; ++q) {
+        const int t = y[q] == kEmpty ? -1 : hlookup(hkey, hpos, 128, y[q]);
+        const uint32_t r = row[q];
+        warp_set_bits(adj, 1, t >= 0, r, t >= 0 ? (uint32_t)t : 0u);
+        if (PV && t >= 0) atomicOr((unsigned long long *)&adj[t], 1ull << r);
       }
     }
   }
   __syncwarp();
   MatView V;
-  V.rows = rows;
-  V.sym = sym;
+  V.adj = adj;
   V.cnt = cnt;
   V.RS = 1;
   V.W = 1;
   unsigned long long rsum = 0;
   if (k == 3) {
     for (uint32_t i = lane; i < d; i += 32) {
-      const unsigned c = (unsigned)__popcll(rows[i]);
+      const uint64_t v = adj[i];
+      const unsigned c = (unsigned)__popcll(v & above_word(i, 0));
       rsum = add_ck(rsum, c, ovf);
-      if (PV) cnt[i] += (unsigned)__popcll(sym[i]);
+      if (PV) cnt[i] = (unsigned)__popcll(v);
       if (PA) asub[i] = c;
     }
   } else {
     uint32_t nitems = d;
     if (k >= 5) {
-      const uint32_t c0 = lane < d ? (uint32_t)__popcll(rows[lane]) : 0u;
-      const uint32_t c1 = lane + 32 < d ? (uint32_t)__popcll(rows[lane + 32]) : 0u;
+      const uint32_t c0 = lane < d ? (uint32_t)__popcll(adj[lane] & above_word(lane, 0)) : 0u;
+      const uint32_t c1 = lane + 32 < d ? (uint32_t)__popcll(adj[lane + 32] & above_word(lane + 32, 0)) : 0u;
       const unsigned y0 = warp_incl_scan(c0), y1 = warp_incl_scan(c1);
       const unsigned t0 = __shfl_sync(0xffffffffu, y0, 31), t1 = __shfl_sync(0xffffffffu, y1, 31);
       pre[lane] = y0 - c0;
@@ -905,7 +1123,7 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
       int ell;
       if (k == 4) {
         i = t;
-        C[0] = rows[i];
+        C[0] = adj[i] & above_word(i, 0);
         ell = 2;
       } else {
         uint32_t lo = 0, hi = d;  // last i with pre[i] <= t
@@ -918,14 +1136,14 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
           atomicOr(a.status, ST_CAPACITY);
           continue;
         }
-        uint64_t w = rows[i];
+        uint64_t w = adj[i] & above_word(i, 0);
         for (uint32_t q = t - pre[i]; q; --q) w &= w - 1;
         if (!w) {
           atomicOr(a.status, ST_CAPACITY);
           continue;
         }
         jv = (uint32_t)(__ffsll((long long)w) - 1);
-        C[0] = rows[i] & rows[jv];
+        C[0] = adj[i] & adj[jv] & above_word(jv, 0);
         ell = k - 3;
       }
       if (__popcll(C[0]) < ell) continue;
@@ -948,6 +1166,8 @@ __device__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigne
     for (uint32_t i = lane; i < d; i += 32) a.pa[b + i] = asub[i];
   tsum = add_ck(tsum, rsum, ovf);
   __syncwarp();
+  ovf_out |= ovf;
+  tsum_out = add_ck(tsum_out, tsum, ovf_out);
 }
 
 template <bool PV, bool PA>
@@ -969,7 +1189,6 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
   }
   finish_block(a, tsum, ovf, red, kWarps);
 }
-
 
 template <bool PV, bool PA>
 cudaError_t occupancy_variant(size_t block_smem, int *block_per_sm, int *warp_per_sm) {

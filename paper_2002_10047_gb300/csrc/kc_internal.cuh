@@ -32,30 +32,31 @@ __host__ __device__ inline uint32_t hash_slots(uint32_t d) {
   return t;
 }
 
+// Positions inside N+(u) follow the total order (out-lists are sorted by
+// rank), so an arc between positions i < t always points from i to t and one
+// symmetric bit matrix holds both directions.
+//
 // Per-root working set of a block-level root with out-degree d:
-//   L      uint32[d]        N+(u)
+//   L      uint32[d]        N+(u), in rank order
 //   rb, rl uint64/uint32[d] start and length of N+(L[i]) in the DAG
-//   hkey   uint32[T]        open-addressing table: vertex id -> position in L
-//   hpos   uint16[T]
-//   rows   uint64[d*W]      the induced subgraph on N+(u), row i = N+(L[i]) within N+(u)
-//   colT   uint64[d*W]      rows | transposed rows (per-vertex counts, k >= 4)
+//   hslot  uint64[T]        open-addressing table: (vertex id << 16 | position in L)
+//   adj    uint64[d*W]      the DAG induced on N+(u), symmetric: bit t of row i
+//                           <=> L[i] and L[t] adjacent (i < t: arc i -> t)
 //   cnt    uint64[d]        per-vertex counters (per-vertex only)
 //   asub   uint64[d]        per-arc sums (per-arc only)
-//   pre    uint32[d+1]      prefix of split-arc sizes (k >= 5)
+//   pre    uint32[d+1]      prefix of split-arc sizes (k >= 6)
 struct RootLayout {
-  size_t L, rb, rl, hkey, hpos, rows, colT, cnt, asub, pre, bytes;
+  size_t L, rb, rl, hslot, adj, cnt, asub, pre, bytes;
 };
-__host__ __device__ inline RootLayout root_layout(uint32_t d, bool pv, bool pa, bool colT) {
+__host__ __device__ inline RootLayout root_layout(uint32_t d, bool pv, bool pa) {
   RootLayout o;
   const uint32_t W = words_of(d), T = hash_slots(d);
   size_t off = 0;
   o.L = off; off += align16((size_t)d * 4);
   o.rb = off; off += align16((size_t)d * 8);
   o.rl = off; off += align16((size_t)d * 4);
-  o.hkey = off; off += align16((size_t)T * 4);
-  o.hpos = off; off += align16((size_t)T * 2);
-  o.rows = off; off += align16((size_t)d * W * 8);
-  o.colT = off; if (colT) off += align16((size_t)d * W * 8);
+  o.hslot = off; off += align16((size_t)T * 8);
+  o.adj = off; off += align16((size_t)d * W * 8);
   o.cnt = off; if (pv) off += align16((size_t)d * 8);
   o.asub = off; if (pa) off += align16((size_t)d * 8);
   o.pre = off; off += align16(((size_t)d + 1) * 4);
@@ -64,19 +65,19 @@ __host__ __device__ inline RootLayout root_layout(uint32_t d, bool pv, bool pa, 
 }
 
 // Per-warp slot of the block-root kernel (item scratch): mask words and their
-// prefix counts, the positions of the compacted vertices, the compacted rows
-// and their symmetric closure, and local per-vertex counters.
+// prefix counts, the root positions of the compacted vertices, the compacted
+// symmetric rows, and local per-vertex counters.
 struct SlotLayout {
-  size_t mask, pfx, P, S, ST, cs, bytes;
+  size_t mask, pfx, P, S, cs, bytes;
 };
 __host__ __device__ inline SlotLayout slot_layout(bool pv) {
   SlotLayout o;
   size_t off = 0;
   o.mask = off; off += 32 * 8;
-  o.pfx = off; off += 32 * 4;
+  o.pfx = off; off += 33 * 4;
+  off = align16(off);
   o.P = off; off += align16(kCompactMax * 2);
   o.S = off; off += kCompactMax * 2 * 8;
-  o.ST = off; if (pv) off += kCompactMax * 2 * 8;
   o.cs = off; if (pv) off += kCompactMax * 8;
   o.bytes = align16(off);
   return o;
@@ -84,7 +85,7 @@ __host__ __device__ inline SlotLayout slot_layout(bool pv) {
 
 // Per-warp slot of the warp-root kernel (roots with d+ <= 64).
 struct LightLayout {
-  size_t L, rb, hkey, hpos, rows, colT, cnt, asub, pre, epre, bytes;
+  size_t L, rb, hkey, hpos, adj, cnt, asub, pre, epre, bytes;
 };
 __host__ __device__ inline LightLayout light_layout(bool pv, bool pa) {
   LightLayout o;
@@ -93,8 +94,7 @@ __host__ __device__ inline LightLayout light_layout(bool pv, bool pa) {
   o.rb = off; off += kLightMax * 8;
   o.hkey = off; off += 128 * 4;
   o.hpos = off; off += 128 * 2;
-  o.rows = off; off += kLightMax * 8;
-  o.colT = off; if (pv) off += kLightMax * 8;
+  o.adj = off; off += kLightMax * 8;
   o.cnt = off; if (pv) off += kLightMax * 8;
   o.asub = off; if (pa) off += kLightMax * 8;
   o.pre = off; off += align16((kLightMax + 1) * 4);
@@ -126,8 +126,8 @@ struct CountArgs {
 void note_launch(unsigned n = 1);
 
 // Launch helpers implemented in kc_count.cu / kc_orient.cu
-size_t block_root_smem(uint32_t dsmem, bool pv, bool pa, bool colT);
-uint32_t block_root_capacity(size_t smem_budget, bool pv, bool pa, bool colT);
+size_t block_root_smem(uint32_t dsmem, bool pv, bool pa);
+uint32_t block_root_capacity(size_t smem_budget, bool pv, bool pa);
 cudaError_t launch_count(const CountArgs &a, bool pv, bool pa, int block_grid, int warp_grid, size_t block_smem,
                          cudaStream_t s);
 cudaError_t count_occupancy(bool pv, bool pa, size_t block_smem, int *block_per_sm, int *warp_per_sm);

@@ -88,9 +88,9 @@ extern "C" kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t budget = (size_t)(optin > 4096 ? optin - 2048 : 48 * 1024);
-  const uint32_t dcap = kc::block_root_capacity(budget, false, false, false);
+  const uint32_t dcap = kc::block_root_capacity(budget, false, false);
   const uint32_t dsmem = std::min<uint32_t>(dcap, std::max<uint32_t>(d->max_out, kc::kLightMax + 1));
-  const size_t block_smem = kc::block_root_smem(dsmem, false, false, false);
+  const size_t block_smem = kc::block_root_smem(dsmem, false, false);
   int per_sm_b = 0, per_sm_w = 0;
   if (kc::count_occupancy(false, false, block_smem, &per_sm_b, &per_sm_w) != cudaSuccess) return KC_ECUDA;
   const int sms = sm_count_here();
@@ -112,7 +112,7 @@ extern "C" kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total,
   a.status = (unsigned *)(b + 8);
   a.queue = (unsigned *)(b + 16);
   if (a.n_scratch > 0) {
-    const size_t slab = (kc::root_layout(d->max_out, false, false, false).bytes + 255) & ~(size_t)255;
+    const size_t slab = (kc::root_layout(d->max_out, false, false).bytes + 255) & ~(size_t)255;
     const size_t room = (size_t)KC_NOALLOC_SCRATCH_BYTES - 256;
     if (slab > room) return KC_ECAPACITY;  // one root's matrix does not fit the static scratch
     size_t nb = room / slab;

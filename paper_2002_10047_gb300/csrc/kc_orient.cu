@@ -251,39 +251,28 @@ __global__ void degree_from_dag_kernel(const uint64_t *__restrict__ dp, const ui
 }
 
 // ------------------------------------------------------------- statistics
+// sum over roots of d+(u)^2 and over arcs u->v of d+(v)
 __global__ void __launch_bounds__(kBlock) dag_stats_kernel(const uint64_t *__restrict__ dp,
                                                            const uint32_t *__restrict__ dc, uint32_t n,
-                                                           unsigned long long *acc /*3*/) {
+                                                           unsigned long long *acc /*2*/) {
   const size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
   const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
   const unsigned lane = lane_id();
-  unsigned long long sq = 0, head = 0, tri = 0;
+  unsigned long long sq = 0, head = 0;
   for (size_t u = warp; u < n; u += nwarps) {
     const uint64_t ub = dp[u], ue = dp[u + 1];
     const uint64_t du = ue - ub;
     if (lane == 0) sq += du * du;
-    for (uint64_t a = ub; a < ue; ++a) {
+    for (uint64_t a = ub + lane; a < ue; a += 32) {
       const uint32_t v = dc[a];
-      const uint64_t vb = dp[v], ve = dp[v + 1];
-      if (lane == 0) head += ve - vb;
-      for (uint64_t j = vb + lane; j < ve; j += 32) {
-        const uint32_t y = dc[j];
-        uint64_t lo = ub, hi = ue;
-        while (lo < hi) {
-          const uint64_t mid = (lo + hi) >> 1;
-          if (dc[mid] < y) lo = mid + 1; else hi = mid;
-        }
-        tri += (lo < ue && dc[lo] == y);
-      }
+      head += dp[v + 1] - dp[v];
     }
   }
   sq = warp_sum(sq);
   head = warp_sum(head);
-  tri = warp_sum(tri);
   if (lane == 0) {
     atomicAdd(&acc[0], sq);
     atomicAdd(&acc[1], head);
-    atomicAdd(&acc[2], tri);
   }
 }
 

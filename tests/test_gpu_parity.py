@@ -33,6 +33,22 @@ def gpu_orient(kc, g, method="degree", sym=False):
     return kc.orient(rp, col, g.n, method=method, validate_symmetry=sym)
 
 
+def rank_ordered(od):
+    """The oracle's out-lists re-sorted into its total order (the library's export order)."""
+    src = np.repeat(np.arange(od.n), np.diff(od.ptr.astype(np.int64)))
+    order = np.lexsort((od.rank[od.adj.astype(np.int64)], src))
+    return od.adj[order]
+
+
+def exported_arcs(dag):
+    """(src, dst) of every arc of the device DAG, in export order."""
+    ptr, col = dag.export()
+    ptr = ptr.cpu().numpy().view(np.uint64)
+    col = col.cpu().numpy().view(np.uint32)
+    src = np.repeat(np.arange(len(ptr) - 1), np.diff(ptr.astype(np.int64)))
+    return ptr, col, src
+
+
 def planted_graph(n=3000, p=0.004, sizes=(40, 70, 100), seed=17):
     eu, ev = gg.erdos_renyi_edges(n, p, seed)
     sets = gg.planted_sets(n, len(sizes), min(sizes), max(sizes), seed + 1)
@@ -71,7 +87,7 @@ def test_orientation_bit_exact(kc, graphs, name, method):
     ptr, col = dag.export()
     assert dag.n == g.n and dag.m == g.m
     np.testing.assert_array_equal(ptr.cpu().numpy().view(np.uint64), od.ptr)
-    np.testing.assert_array_equal(col.cpu().numpy().view(np.uint32), od.adj)
+    np.testing.assert_array_equal(col.cpu().numpy().view(np.uint32), rank_ordered(od))
     assert dag.max_out_degree == int(np.diff(od.ptr.astype(np.int64)).max(initial=0))
 
 
@@ -94,7 +110,7 @@ def test_per_arc_bit_exact(kc, graphs, name):
     g = graphs[name]
     dag = gpu_orient(kc, g, "degree")
     odag = oracle.orient(g, "degree")
-    src = np.repeat(np.arange(odag.n), np.diff(odag.ptr.astype(np.int64)))
+    _, col, src = exported_arcs(dag)
     rng = np.random.default_rng(5)
     pick = rng.choice(odag.m, size=min(400, odag.m), replace=False)
     for k in (2, 3, 4, 5):
@@ -102,7 +118,20 @@ def test_per_arc_bit_exact(kc, graphs, name):
         pa = kc.as_uint64(pa)
         assert int(pa.sum()) == tot == oracle.count(odag, k, threads=8)
         for e in pick:
-            assert int(pa[e]) == oracle.count_arc(odag, k, int(src[e]), int(odag.adj[e])), (name, k, e)
+            assert int(pa[e]) == oracle.count_arc(odag, k, int(src[e]), int(col[e])), (name, k, e)
+
+
+def test_dag_stats(kc, graphs):
+    for name in ("rmat12", "planted", "turan"):
+        g = graphs[name]
+        dag = gpu_orient(kc, g, "degree")
+        st = kc.dag_stats(dag)
+        ptr, col, src = exported_arcs(dag)
+        dout = np.diff(ptr.astype(np.int64))
+        assert st["max_out"] == int(dout.max(initial=0))
+        assert st["sum_out_sq"] == int((dout * dout).sum())
+        assert st["sum_arc_head"] == int(dout[col.astype(np.int64)].sum())
+        assert st["triangles"] == oracle.count(oracle.orient(g, "degree"), 3)
 
 
 def test_gp_orientation_counts(kc, graphs):
@@ -218,11 +247,9 @@ def test_config_rmat20_sampled(kc):
     k = 4, 5 with every output; k = 6 per-arc only (k = 7 is exercised by the bench)."""
     g = gg.config_rmat20()
     dag = gpu_orient(kc, g, "degree")
-    ptr, col = dag.export()
-    ptr = ptr.cpu().numpy().view(np.uint64)
-    col = col.cpu().numpy().view(np.uint32)
-    odag = oracle.Dag(g.n, ptr, col, None)
-    src = np.repeat(np.arange(g.n), np.diff(ptr.astype(np.int64)))
+    ptr, col, src = exported_arcs(dag)
+    # the oracle intersects out-lists sorted by id
+    odag = oracle.Dag(g.n, ptr, np.ascontiguousarray(col[np.lexsort((col, src))]), None)
     rng = np.random.default_rng(20)
     pick = rng.choice(odag.m, size=300, replace=False)
     s3 = {int(e): oracle.count_arc(odag, 3, int(src[e]), int(col[e])) for e in pick}
