@@ -229,7 +229,7 @@ __device__ __forceinline__ unsigned long long leaf2(const uint64_t (&C)[NW], con
                                                     unsigned &ovf_out) {
   unsigned ovf = 0;
   unsigned long long acc = 0;
-  if constexpr (G == 1 && NW <= 2) {
+  if constexpr (G == 1 && !PV) {
 #pragma unroll
     for (int r = 0; r < NW; ++r) {
       uint64_t t = C[r];
@@ -237,48 +237,11 @@ __device__ __forceinline__ unsigned long long leaf2(const uint64_t (&C)[NW], con
         const int x = r * 64 + __ffsll((long long)t) - 1;
         t &= t - 1;
         const uint64_t *row = V.adj + (size_t)x * V.RS;
-        unsigned a = 0;
-        if (PV) {
+        unsigned a = __popcll(t & row[r]);
 #pragma unroll
-          for (int q = 0; q < NW; ++q) a += __popcll(C[q] & row[q]);
-          if (a) atomic_add_ck(&V.cnt[x], a, ovf);
-        } else {
-          a = __popcll(t & row[r]);
-#pragma unroll
-          for (int q = r + 1; q < NW; ++q) a += __popcll(C[q] & row[q]);
-        }
+        for (int q = r + 1; q < NW; ++q) a += __popcll(C[q] & row[q]);
         acc += a;
       }
-    }
-  } else if constexpr (G == 1) {
-    // wide sets: one loop body, the next member found branch-free; the count
-    // reads only the words at or above the member's word
-    uint64_t T[NW];
-#pragma unroll
-    for (int r = 0; r < NW; ++r) T[r] = C[r];
-    for (;;) {
-      int x = -1;
-#pragma unroll
-      for (int r = 0; r < NW; ++r) {
-        if (x < 0 && T[r]) {
-          x = r * 64 + __ffsll((long long)T[r]) - 1;
-          T[r] &= T[r] - 1;
-        }
-      }
-      if (x < 0) break;
-      const uint64_t *row = V.adj + (size_t)x * V.RS;
-      const int rx = x >> 6;
-      unsigned a = 0;
-      if (PV) {
-#pragma unroll
-        for (int q = 0; q < NW; ++q) a += __popcll(C[q] & row[q]);
-        if (a) atomic_add_ck(&V.cnt[x], a, ovf);
-      } else {
-#pragma unroll
-        for (int q = 0; q < NW; ++q)
-          if (q >= rx) a += __popcll(T[q] & row[q]);
-      }
-      acc += a;
     }
   } else {
     uint64_t T[NW];
