@@ -187,6 +187,16 @@ typedef struct {
 } kc_dag_stats;
 kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t stream);
 
+/*
+ * Measured rate of the counting kernels' unit of integer work on the current
+ * device: one 64-bit AND followed by a population count (the bitset form of
+ * the intersect of Algorithm 1). Used as the roofline peak of the counting
+ * passes for k >= 5, which are bound by this work. Runs a short calibration
+ * kernel (about 10 ms) on `stream` and synchronises it.
+ *   h_rate  receives word operations per second
+ */
+kc_status kc_measure_word_op_rate(double *h_rate, kc_stream_t stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all entry points, all devices). For accounting in benchmarks. */
 uint64_t kc_kernel_launches(void);

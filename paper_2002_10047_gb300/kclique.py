@@ -84,6 +84,8 @@ def _load():
         lib.kc_count_per_vertex.argtypes = [P, I, P, P, P]
         lib.kc_count_per_arc.argtypes = [P, I, P, P, P]
         lib.kc_dag_get_stats.argtypes = [P, ctypes.POINTER(_Stats), P]
+        lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
+        lib.kc_measure_word_op_rate.restype = I
         lib.kc_kernel_launches.argtypes = []
         lib.kc_kernel_launches.restype = U64
         lib.kc_strerror.argtypes = [I]
@@ -216,6 +218,13 @@ def kc_dag_get_stats(dag: Dag, stream=None) -> dict:
     _check(_load().kc_dag_get_stats(dag.handle, ctypes.byref(st), _stream(stream)))
     return {"sum_out_sq": int(st.sum_out_sq), "sum_arc_head": int(st.sum_arc_head),
             "triangles": int(st.triangles), "max_out": int(st.max_out)}
+
+
+def kc_measure_word_op_rate(stream=None) -> float:
+    """Measured 64-bit AND + popcount operations per second on the current device."""
+    r = ctypes.c_double()
+    _check(_load().kc_measure_word_op_rate(ctypes.byref(r), _stream(stream)))
+    return float(r.value)
 
 
 def kc_kernel_launches() -> int:
