@@ -171,6 +171,94 @@ kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_
 kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total, kc_stream_t stream);
 
 /*
+ * Batches of many small graphs (the paper counts one graph per call; this is
+ * the many-graph form of the same arb-count pass, for workloads of thousands
+ * of uneven graphs).
+ *
+ * A batch is one kc_dag oriented from the disjoint union of the graphs: graph
+ * g owns the vertex ids [off[g], off[g+1]) of the union CSR (concatenate the
+ * graphs' CSRs, shifting each graph's ids by off[g]) and has its own clique
+ * size k[g]. Since no arc joins two graphs, the union's k-cliques rooted in
+ * graph g are exactly graph g's k[g]-cliques, so all graphs are counted by one
+ * pass of the persistent kernels, each root with its own graph's k.
+ *   num_graphs        >= 1
+ *   d_vertex_offsets  device uint64[num_graphs+1], off[0] = 0,
+ *                     non-decreasing, off[num_graphs] = n of the union
+ *   d_k               device uint8[num_graphs], each in [3, KC_KMAX]
+ *                     (k = 1 and 2 are the graph's n and m)
+ *   k_min             smallest value in d_k (roots with fewer than k_min-1
+ *                     out-neighbours are skipped without being visited)
+ * If arcs do join two graphs, total[g] counts the cliques whose lowest vertex
+ * (in the total order of the orientation) lies in graph g.
+ */
+typedef struct {
+  uint32_t num_graphs;
+  const uint64_t *d_vertex_offsets;
+  const uint8_t *d_k;
+  uint8_t k_min;
+} kc_batch;
+
+/*
+ * Tunables of a counting pass (0 in a field = the built-in default):
+ *   light_max    warp/block split: roots with out-degree <= light_max are
+ *                counted by one warp, larger ones by one 512-thread block
+ *                (2 .. 64; default 64)
+ *   compact_max  bitset width of the compacted sub-problems: candidate sets
+ *                of at most this many vertices are renumbered into a 1- or
+ *                2-word (64- or 128-bit) bit matrix (1 .. 128; default 128)
+ *   chunk        roots a warp takes per pull from the atomic work queue of
+ *                the warp kernel (default 1)
+ * Every setting gives the same counts; only the speed differs.
+ */
+typedef struct {
+  uint32_t light_max;
+  uint32_t compact_max;
+  uint32_t chunk;
+} kc_params;
+
+/*
+ * kc_count_batched -- the k[g]-clique count of every graph of a batch.
+ *   d         kc_orient of the union CSR (see kc_batch)
+ *   prm       tunables or NULL
+ *   d_totals  device uint64[num_graphs], caller-owned, overwritten
+ *   h_total   optional: receives the sum over all graphs
+ * Allocates and frees its work space; synchronises `stream`. KC_EINVAL if
+ * a d_k entry lies outside [3, KC_KMAX] (detected on the device).
+ */
+kc_status kc_count_batched(const kc_dag *d, const kc_batch *b, const kc_params *prm, uint64_t *d_totals,
+                           uint64_t *h_total, kc_stream_t stream);
+
+/*
+ * A prepared batched pass for repeated, capturable launches: kc_plan_create
+ * sizes the kernels for (d, b, prm), allocates the work block and any global
+ * scratch, and keeps the pointers (d, b's arrays and d_totals must stay valid
+ * while the plan lives). kc_plan_launch only enqueues work on `stream`: two
+ * memsets (totals and work block) and the counting kernels, with no
+ * allocation and no synchronisation, so it may be recorded into a CUDA graph
+ * by stream capture and replayed. kc_plan_result copies the work block back,
+ * synchronises `stream` and maps the device status of the last completed
+ * launch to a kc_status (h_total, optional, receives the sum over graphs).
+ * One plan's launches must not overlap on the GPU (they share its work
+ * block); distinct plans are independent.
+ */
+typedef struct kc_plan kc_plan;
+kc_status kc_plan_create(const kc_dag *d, const kc_batch *b, const kc_params *prm, uint64_t *d_totals,
+                         kc_plan **out, kc_stream_t stream);
+kc_status kc_plan_launch(kc_plan *p, kc_stream_t stream);
+kc_status kc_plan_result(kc_plan *p, uint64_t *h_total, kc_stream_t stream);
+void kc_plan_free(kc_plan *p);
+
+/*
+ * kc_autotune_batched -- the tunables (light_max, compact_max, chunk) that
+ * count the batch fastest on this device: times each candidate of a small
+ * grid (two launches each, CUDA events, after one warm-up launch) and writes
+ * the fastest to *out; *h_best_ms (optional) receives its time. d_totals is
+ * used as the output of the trial passes. Synchronises `stream`.
+ */
+kc_status kc_autotune_batched(const kc_dag *d, const kc_batch *b, uint64_t *d_totals, kc_params *out,
+                              float *h_best_ms, kc_stream_t stream);
+
+/*
  * Work statistics of an oriented graph, used for the bytes a counting pass
  * must move (computed exactly on the device):
  *   sum_out_sq     sum over roots u of d+(u)^2

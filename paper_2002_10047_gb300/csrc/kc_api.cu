@@ -17,48 +17,21 @@
 
 #include <atomic>
 
+#include "kc_host.cuh"
+
 namespace kc {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
-}  // namespace kc
 
 namespace {
-
 thread_local std::string g_cuda_err;
+}
 
 kc_status cuda_fail(cudaError_t e) {
   g_cuda_err = cudaGetErrorString(e);
   if (e == cudaErrorMemoryAllocation) return KC_ENOMEM;
   return KC_ECUDA;
 }
-
-#define KC_CK(call)                               \
-  do {                                            \
-    cudaError_t e_ = (call);                      \
-    if (e_ != cudaSuccess) return cuda_fail(e_);  \
-  } while (0)
-
-// Stream-ordered device buffers released when the scope ends.
-struct DevBuf {
-  void *p = nullptr;
-  cudaStream_t s = nullptr;
-  ~DevBuf() {
-    if (p) cudaFreeAsync(p, s);
-  }
-  cudaError_t alloc(size_t bytes, cudaStream_t st) {
-    s = st;
-    return cudaMallocAsync(&p, bytes ? bytes : 16, st);
-  }
-  template <typename T>
-  T *as() const {
-    return (T *)p;
-  }
-  void *release() {
-    void *q = p;
-    p = nullptr;
-    return q;
-  }
-};
 
 int sm_count() {
   int dev = 0, n = 0;
@@ -67,12 +40,17 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
-}  // namespace
-
-namespace kc {
-kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned long long *pa, uint64_t *h_total,
-                    uint64_t deadline_ns, cudaStream_t s);
+kc_status status_code(unsigned st) {
+  if (st & ST_CAPACITY) return KC_ECAPACITY;
+  if (st & ST_OVERFLOW) return KC_ERANGE;
+  if (st & ST_TIMEOUT) return KC_ETIMEDOUT;
+  if (st & ST_BAD_ARG) return KC_EINVAL;
+  return KC_OK;
+}
 }  // namespace kc
+
+using kc::DevBuf;
+using kc::cuda_fail;
 
 extern "C" {
 
@@ -89,7 +67,7 @@ const char *kc_strerror(int status) {
   }
 }
 
-const char *kc_last_cuda_error(void) { return g_cuda_err.c_str(); }
+const char *kc_last_cuda_error(void) { return kc::g_cuda_err.c_str(); }
 
 uint64_t kc_kernel_launches(void) { return kc::g_launches.load(std::memory_order_relaxed); }
 
@@ -234,6 +212,61 @@ kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t s
 
 namespace kc {
 
+size_t kc_work_bytes() { return 64; }
+
+// total at +0, status word at +8, the three root queues at +16
+void set_work(CountArgs *a, uint8_t *w) {
+  a->total = (unsigned long long *)w;
+  a->status = (unsigned *)(w + 8);
+  a->queue = (unsigned *)(w + 16);
+}
+
+// Kernel configuration for a counting pass over d with smallest k = k_min:
+// shared-memory capacity of a block root, grids from the occupancy, the root
+// ranges of the order array, and the global scratch the largest roots need.
+cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_params *prm, LaunchPlan *out) {
+  LaunchPlan &P = *out;
+  memset(&P, 0, sizeof P);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t budget = (size_t)(optin > 4096 ? optin - 2048 : 48 * 1024);
+  const uint32_t dcap = block_root_capacity(budget, pv, pa);
+  uint32_t light = prm && prm->light_max ? prm->light_max : (uint32_t)kLightMax;
+  if (light > (uint32_t)kLightMax) light = kLightMax;
+  if (light < 2) light = 2;
+  const uint32_t dsmem = std::min<uint32_t>(dcap, std::max<uint32_t>(d->max_out, light + 1));
+  P.block_smem = block_root_smem(dsmem, pv, pa);
+  int per_sm_b = 0, per_sm_w = 0;
+  cudaError_t e = count_occupancy(pv, pa, P.block_smem, &per_sm_b, &per_sm_w);
+  if (e != cudaSuccess) return e;
+  const int sms = sm_count();
+  P.block_grid = sms * std::max(1, per_sm_b);
+  P.warp_grid = sms * std::max(1, per_sm_w);
+  CountArgs &a = P.a;
+  a.ptr = d->ptr;
+  a.col = d->col;
+  a.order = d->order;
+  a.k = k_min;
+  auto ge = [&](uint64_t t) -> uint32_t { return t < d->ge.size() ? (uint32_t)d->ge[t] : 0u; };
+  a.n_light_end = ge((uint64_t)(k_min - 1));
+  a.n_big = ge((uint64_t)light + 1);
+  a.n_scratch = ge((uint64_t)dcap + 1);
+  a.compact_max = prm ? prm->compact_max : 0;
+  a.chunk = prm ? prm->chunk : 0;
+  if (a.n_scratch > 0) {
+    const size_t slab = (root_layout(d->max_out, pv, pa).bytes + 255) & ~(size_t)255;
+    const size_t sbudget = (size_t)4 << 30;
+    size_t nb = std::max<size_t>(1, sbudget / slab);
+    nb = std::min<size_t>(nb, (size_t)P.block_grid);
+    nb = std::min<size_t>(nb, (size_t)a.n_scratch);
+    a.scratch_stride = slab;
+    a.scratch_blocks = (uint32_t)nb;
+    P.scratch_bytes = slab * nb;
+  }
+  return cudaSuccess;
+}
+
 // Shared driver of kc_count / kc_count_per_vertex / kc_count_per_arc.
 kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned long long *pa, uint64_t *h_total,
                     uint64_t deadline_ns, cudaStream_t s) {
@@ -262,61 +295,26 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
     return KC_OK;
   }
   if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
-  const bool bpv = pv != nullptr, bpa = pa != nullptr;
-
-  // shared memory of a block root: per-warp item slots + the root's matrix
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  const size_t budget = (size_t)(optin > 4096 ? optin - 2048 : 48 * 1024);
-  const uint32_t dcap = block_root_capacity(budget, bpv, bpa);
-  const uint32_t dsmem = std::min<uint32_t>(dcap, std::max<uint32_t>(d->max_out, kLightMax + 1));
-  const size_t block_smem = block_root_smem(dsmem, bpv, bpa);
-  int per_sm_b = 0, per_sm_w = 0;
-  KC_CK(count_occupancy(bpv, bpa, block_smem, &per_sm_b, &per_sm_w));
-  const int sms = sm_count();
-  const int block_grid = sms * std::max(1, per_sm_b);
-  const int warp_grid = sms * std::max(1, per_sm_w);
-
-  CountArgs a;
-  memset(&a, 0, sizeof a);
-  a.ptr = d->ptr;
-  a.col = d->col;
-  a.order = d->order;
-  a.k = k;
-  auto ge = [&](uint64_t t) -> uint32_t { return t < d->ge.size() ? (uint32_t)d->ge[t] : 0u; };
-  a.n_light_end = ge(need);
-  a.n_big = ge(kLightMax + 1);
-  a.n_scratch = ge((uint64_t)dcap + 1);
+  LaunchPlan P;
+  KC_CK(plan_count(d, k, pv != nullptr, pa != nullptr, nullptr, &P));
+  CountArgs &a = P.a;
   a.pv = pv;
   a.pa = pa;
   a.deadline_ns = deadline_ns;
-
   DevBuf work, scratch;
-  KC_CK(work.alloc(64, s));
-  KC_CK(cudaMemsetAsync(work.p, 0, 64, s));
-  a.total = work.as<unsigned long long>();
-  a.status = (unsigned *)(work.as<uint8_t>() + 8);
-  a.queue = (unsigned *)(work.as<uint8_t>() + 16);
-  if (a.n_scratch > 0) {
-    const size_t slab = (root_layout(d->max_out, bpv, bpa).bytes + 255) & ~(size_t)255;
-    const size_t sbudget = (size_t)4 << 30;
-    size_t nb = std::max<size_t>(1, sbudget / slab);
-    nb = std::min<size_t>(nb, (size_t)block_grid);
-    nb = std::min<size_t>(nb, (size_t)a.n_scratch);
-    KC_CK(scratch.alloc(slab * nb, s));
+  KC_CK(work.alloc(kc_work_bytes(), s));
+  KC_CK(cudaMemsetAsync(work.p, 0, kc_work_bytes(), s));
+  set_work(&a, work.as<uint8_t>());
+  if (P.scratch_bytes) {
+    KC_CK(scratch.alloc(P.scratch_bytes, s));
     a.scratch = scratch.as<uint8_t>();
-    a.scratch_stride = slab;
-    a.scratch_blocks = (uint32_t)nb;
   }
-  KC_CK(launch_count(a, bpv, bpa, block_grid, warp_grid, block_smem, s));
+  KC_CK(launch_count(a, pv != nullptr, pa != nullptr, P.block_grid, P.warp_grid, P.block_smem, s));
   unsigned long long h[2] = {0, 0};
   KC_CK(cudaMemcpyAsync(h, work.p, sizeof h, cudaMemcpyDeviceToHost, s));
   KC_CK(cudaStreamSynchronize(s));
-  const unsigned st = (unsigned)h[1];
-  if (st & ST_CAPACITY) return KC_ECAPACITY;
-  if (st & ST_OVERFLOW) return KC_ERANGE;
-  if (st & ST_TIMEOUT) return KC_ETIMEDOUT;
+  const kc_status code = status_code((unsigned)h[1]);
+  if (code != KC_OK) return code;
   if (h_total) *h_total = h[0];
   return KC_OK;
 }

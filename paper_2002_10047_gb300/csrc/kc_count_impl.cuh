@@ -670,6 +670,16 @@ __device__ unsigned long long k4_item(const MatView M, uint32_t s, const Slot sl
   { const auto ret_ = (warp_sum64_ck(acc, ovf)); ovf_out |= ovf; return ret_; }
 }
 
+// graph of vertex u in a batch (last g with goff[g] <= u), and its k
+__device__ __forceinline__ uint32_t graph_of(const CountArgs &a, uint32_t u) {
+  uint32_t lo = 0, hi = a.ngraphs - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (a.goff[mid] <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 // ------------------------------------------------------- block-level root
 struct BlockShared {
   unsigned long long red[kRootWarps];
@@ -701,7 +711,14 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
   const uint64_t b = a.ptr[u];
   const uint32_t d = (uint32_t)(a.ptr[u + 1] - b);
   const uint32_t W = words_of(d), T = hash_slots(d);
-  const int k = a.k;
+  const uint32_t g = a.goff ? graph_of(a, u) : 0u;
+  const int k = a.goff ? (int)a.gk[g] : a.k;
+  if (k < 3 || k > KC_KMAX) {  // batches only: k = 1, 2 have closed forms, larger k is rejected
+    if ((threadIdx.x & 31) == 0) atomicOr(a.status, ST_BAD_ARG);
+    return;
+  }
+  if (d + 1 < (uint32_t)k) return;  // the root cannot hold a k-clique
+  const uint32_t cmax = a.compact_max ? min(a.compact_max, (uint32_t)kCompactMax) : (uint32_t)kCompactMax;
   const RootLayout lay = root_layout(d, PV, PA);
   uint32_t *L = (uint32_t *)(base + lay.L);
   uint64_t *rb = (uint64_t *)(base + lay.rb);
@@ -800,7 +817,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
       for (uint32_t i = c0; i < c1; ++i) {
         unsigned c = 0;
         for (uint32_t w = 0; w < W; ++w) c += (unsigned)__popcll(adj[(size_t)i * W + w] & above_word(i, w));
-        c = c > (unsigned)kCompactMax ? c : 0u;
+        c = c > cmax ? c : 0u;
         pre[i] = c;
         cl += c;
       }
@@ -841,9 +858,9 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
           if (s >= (uint32_t)(k - 2)) {
             if (k == 4) {
               item = k4_item<PV>(M, s, sl, ovf);
-            } else if (k == 5 && (W <= 2 || s > (uint32_t)kCompactMax)) {
+            } else if (k == 5 && (W <= 2 || s > cmax)) {
               item = split_dispatch<PV>(M, s, 3, sl, ovf);  // one level below: compaction does not pay
-            } else if (s <= (uint32_t)kCompactMax) {
+            } else if (s <= cmax) {
               item = compact_count<PV>(M, s, k - 2, sl, cnt, ovf);
             }  // else (k >= 6): split into pair items
           }
@@ -875,7 +892,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
           const uint64_t mw = lane < W ? (wv & rv[lane] & above_word(av, lane)) : 0ull;
           const uint32_t s0 = slot_set(sl, mw, W);
           if (s0 >= (uint32_t)(k - 3)) {
-            if (s0 <= (uint32_t)kCompactMax) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf);
+            if (s0 <= cmax) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf);
             else item = split_dispatch<PV>(M, s0, k - 3, sl, ovf);
           }
         } else {
@@ -894,16 +911,18 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
     }
   }
   __syncthreads();
-  if (PV) {
+  if (PV || a.gtotal) {
     const unsigned long long r = warp_sum64_ck(rsum, ovf);
     if (lane == 0) sh.red[warp] = r;
     __syncthreads();
     if (tid == 0) {
       unsigned long long t = 0;
       for (int w = 0; w < kRootWarps; ++w) t = add_ck(t, sh.red[w], ovf);
-      atomic_add_ck(&a.pv[u], t, ovf);
+      if (PV) atomic_add_ck(&a.pv[u], t, ovf);
+      if (a.gtotal) atomic_add_ck(&a.gtotal[g], t, ovf);
     }
-    for (uint32_t i = tid; i < d; i += kRootBlock) atomic_add_ck(&a.pv[L[i]], cnt[i], ovf);
+    if (PV)
+      for (uint32_t i = tid; i < d; i += kRootBlock) atomic_add_ck(&a.pv[L[i]], cnt[i], ovf);
   }
   if (PA)
     for (uint32_t i = tid; i < d; i += kRootBlock) a.pa[b + i] = asub[i];
@@ -992,7 +1011,13 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_
   uint32_t *epre = (uint32_t *)(slot + o.epre);
   const uint64_t b = a.ptr[u];
   const uint32_t d = (uint32_t)(a.ptr[u + 1] - b);
-  const int k = a.k;
+  const uint32_t g = a.goff ? graph_of(a, u) : 0u;
+  const int k = a.goff ? (int)a.gk[g] : a.k;
+  if (k < 3 || k > KC_KMAX) {  // batches only: k = 1, 2 have closed forms, larger k is rejected
+    if ((threadIdx.x & 31) == 0) atomicOr(a.status, ST_BAD_ARG);
+    return;
+  }
+  if (d + 1 < (uint32_t)k) return;  // the root cannot hold a k-clique
   for (uint32_t i = lane; i < (uint32_t)kLightMax; i += 32) {
     adj[i] = 0;
     if (PV) cnt[i] = 0;
@@ -1120,10 +1145,12 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_
     }
   }
   __syncwarp();
-  if (PV) {
+  if (PV || a.gtotal) {
     const unsigned long long t = warp_sum64_ck(rsum, ovf);
-    if (lane == 0) atomic_add_ck(&a.pv[u], t, ovf);
-    for (uint32_t i = lane; i < d; i += 32) atomic_add_ck(&a.pv[L[i]], cnt[i], ovf);
+    if (lane == 0 && PV) atomic_add_ck(&a.pv[u], t, ovf);
+    if (lane == 0 && a.gtotal) atomic_add_ck(&a.gtotal[g], t, ovf);
+    if (PV)
+      for (uint32_t i = lane; i < d; i += 32) atomic_add_ck(&a.pv[L[i]], cnt[i], ovf);
   }
   if (PA)
     for (uint32_t i = lane; i < d; i += 32) a.pa[b + i] = asub[i];
@@ -1143,12 +1170,14 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
   unsigned long long tsum = 0;
   uint8_t *slot = smem + (size_t)warp * light_layout(PV, PA).bytes;
   const uint32_t nlight = a.n_light_end - a.n_big;
+  const uint32_t chunk = a.chunk ? a.chunk : 1u;
   for (;;) {
     unsigned idx = 0;
-    if (lane == 0) idx = past_deadline(a) ? 0xffffffffu : atomicAdd(&a.queue[2], 1u);
+    if (lane == 0) idx = past_deadline(a) ? 0xffffffffu : atomicAdd(&a.queue[2], chunk);
     idx = __shfl_sync(0xffffffffu, idx, 0);
     if (idx >= nlight) break;
-    warp_root<PV, PA>(a, a.order[a.n_big + idx], slot, tsum, ovf, &w_next[warp]);
+    const uint32_t end = min(nlight, idx + chunk);
+    for (uint32_t q = idx; q < end; ++q) warp_root<PV, PA>(a, a.order[a.n_big + q], slot, tsum, ovf, &w_next[warp]);
   }
   finish_block(a, tsum, ovf, red, kWarps);
 }

@@ -13,6 +13,7 @@ enum : unsigned {
   ST_BAD_CSR = 2u,    // validation failed
   ST_TIMEOUT = 4u,    // deadline / cancel
   ST_CAPACITY = 8u,   // an internal capacity check failed (the access was skipped)
+  ST_BAD_ARG = 16u,   // a per-graph k of a batch outside [3, KC_KMAX]
 };
 
 constexpr int kBlock = 256;              // threads per block of the orientation kernels
@@ -107,9 +108,9 @@ struct CountArgs {
   const uint64_t *ptr;       // DAG offsets, n+1
   const uint32_t *col;       // DAG out-lists, m
   const uint32_t *order;     // roots sorted by out-degree, descending
-  uint32_t n_big;            // order[0, n_big): d+ > kLightMax (block roots)
+  uint32_t n_big;            // order[0, n_big): d+ above the light threshold (block roots)
   uint32_t n_scratch;        // order[0, n_scratch): block roots whose matrices live in global scratch
-  uint32_t n_light_end;      // order[n_big, n_light_end): k-1 <= d+ <= kLightMax (warp roots)
+  uint32_t n_light_end;      // order[n_big, n_light_end): k-1 <= d+ <= light threshold <= kLightMax (warp roots)
   int k;
   unsigned long long *total; // global sum
   unsigned long long *pv;    // per-vertex output (n) or null
@@ -120,6 +121,23 @@ struct CountArgs {
   size_t scratch_stride;     // bytes per slab
   uint32_t scratch_blocks;   // blocks that take scratch roots
   uint64_t deadline_ns;      // globaltimer deadline, 0 = none
+  // batches of disjoint graphs (null for a single graph): graph g owns
+  // vertices [goff[g], goff[g+1]), counts its gk[g]-cliques, sums into gtotal[g]
+  const uint64_t *goff;
+  const uint8_t *gk;
+  unsigned long long *gtotal;
+  uint32_t ngraphs;
+  // tunables (kc_params; 0 = default): largest candidate set compacted
+  // (<= kCompactMax), roots a warp takes per queue pull in the warp-root kernel
+  uint32_t compact_max;
+  uint32_t chunk;
+};
+
+// A configured counting pass (kc_api.cu).
+struct LaunchPlan {
+  CountArgs a;
+  int block_grid, warp_grid;
+  size_t block_smem, scratch_bytes;
 };
 
 // Process-wide count of kernel launches issued by this library.
@@ -131,6 +149,9 @@ uint32_t block_root_capacity(size_t smem_budget, bool pv, bool pa);
 cudaError_t launch_count(const CountArgs &a, bool pv, bool pa, int block_grid, int warp_grid, size_t block_smem,
                          cudaStream_t s);
 cudaError_t count_occupancy(bool pv, bool pa, size_t block_smem, int *block_per_sm, int *warp_per_sm);
+
+size_t kc_work_bytes();
+void set_work(CountArgs *a, uint8_t *w);
 
 cudaError_t exclusive_scan_u32(const uint32_t *in, uint64_t *out, size_t n, uint64_t *tmp, size_t tmp_elems,
                                cudaStream_t s);

@@ -303,6 +303,25 @@ def disjoint_union(graphs) -> Csr:
     return from_edges(off, np.concatenate(us), np.concatenate(vs))
 
 
+def concat_csr(graphs) -> tuple[Csr, np.ndarray]:
+    """Disjoint union by concatenating CSRs: graph g's ids shift by off[g].
+    Rows stay sorted, so this equals disjoint_union without re-sorting.
+    Returns (union, off uint64[len(graphs)+1])."""
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    off = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(ns, out=off[1:])
+    nnz = np.array([g.nnz for g in graphs], dtype=np.int64)
+    eoff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(nnz, out=eoff[1:])
+    col = np.empty(int(eoff[-1]), dtype=np.uint32)
+    row_ptr = np.empty(int(off[-1]) + 1, dtype=np.int64)
+    row_ptr[-1] = eoff[-1]
+    for i, g in enumerate(graphs):
+        np.add(g.col, np.uint32(off[i]), out=col[eoff[i]:eoff[i + 1]], casting="unsafe")
+        np.add(g.row_ptr[:-1].astype(np.int64, copy=False), eoff[i], out=row_ptr[off[i]:off[i + 1]])
+    return Csr(int(off[-1]), row_ptr.view(np.uint64), col), off.astype(np.uint64)
+
+
 def relabel(g: Csr, perm) -> Csr:
     """Graph with vertex v renamed perm[v]."""
     perm = np.asarray(perm, dtype=np.int64)

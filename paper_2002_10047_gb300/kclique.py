@@ -47,6 +47,15 @@ class _Csr(ctypes.Structure):
                 ("d_row_ptr", ctypes.c_void_p), ("d_col", ctypes.c_void_p)]
 
 
+class _Batch(ctypes.Structure):
+    _fields_ = [("num_graphs", ctypes.c_uint32), ("d_vertex_offsets", ctypes.c_void_p),
+                ("d_k", ctypes.c_void_p), ("k_min", ctypes.c_uint8)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("light_max", ctypes.c_uint32), ("compact_max", ctypes.c_uint32), ("chunk", ctypes.c_uint32)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("sum_out_sq", ctypes.c_uint64), ("sum_arc_head", ctypes.c_uint64),
                 ("triangles", ctypes.c_uint64), ("max_out", ctypes.c_uint32)]
@@ -84,6 +93,14 @@ def _load():
         lib.kc_count_per_vertex.argtypes = [P, I, P, P, P]
         lib.kc_count_per_arc.argtypes = [P, I, P, P, P]
         lib.kc_dag_get_stats.argtypes = [P, ctypes.POINTER(_Stats), P]
+        BP, PP = ctypes.POINTER(_Batch), ctypes.POINTER(_Params)
+        lib.kc_count_batched.argtypes = [P, BP, PP, P, ctypes.POINTER(U64), P]
+        lib.kc_plan_create.argtypes = [P, BP, PP, P, ctypes.POINTER(P), P]
+        lib.kc_plan_launch.argtypes = [P, P]
+        lib.kc_plan_result.argtypes = [P, ctypes.POINTER(U64), P]
+        lib.kc_plan_free.argtypes = [P]
+        lib.kc_plan_free.restype = None
+        lib.kc_autotune_batched.argtypes = [P, BP, P, PP, ctypes.POINTER(ctypes.c_float), P]
         lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         lib.kc_measure_word_op_rate.restype = I
         lib.kc_kernel_launches.argtypes = []
@@ -93,7 +110,8 @@ def _load():
         lib.kc_last_cuda_error.argtypes = []
         lib.kc_last_cuda_error.restype = ctypes.c_char_p
         for f in (lib.kc_orient, lib.kc_dag_export, lib.kc_count, lib.kc_count_per_vertex,
-                  lib.kc_count_per_arc, lib.kc_dag_get_stats):
+                  lib.kc_count_per_arc, lib.kc_dag_get_stats, lib.kc_count_batched, lib.kc_plan_create,
+                  lib.kc_plan_launch, lib.kc_plan_result, lib.kc_autotune_batched):
             f.restype = I
         _lib = lib
         return lib
@@ -213,6 +231,91 @@ def kc_count_per_arc(dag: Dag, k: int, out: torch.Tensor | None = None, stream=N
     return int(t.value), out[:dag.m]
 
 
+class Batch:
+    """A batch of disjoint graphs in one oriented union (kc_batch): graph g owns
+    vertices [offsets[g], offsets[g+1]) and counts its ks[g]-cliques."""
+
+    def __init__(self, offsets: torch.Tensor, ks: torch.Tensor):
+        _require_cuda(offsets, "offsets", (torch.int64,))
+        _require_cuda(ks, "ks", (torch.uint8,))
+        if offsets.numel() != ks.numel() + 1 or ks.numel() == 0:
+            raise ValueError("offsets must have num_graphs+1 entries, ks num_graphs >= 1")
+        self.offsets, self.ks = offsets, ks
+        self.num_graphs = ks.numel()
+        self.k_min = int(ks.min().item())
+        self._c = _Batch(self.num_graphs, offsets.data_ptr(), ks.data_ptr(), self.k_min)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+
+def _params(params):
+    if params is None:
+        return None
+    if isinstance(params, dict):
+        params = (params.get("light_max", 0), params.get("compact_max", 0), params.get("chunk", 0))
+    return ctypes.byref(_Params(*[int(x) for x in params]))
+
+
+def _totals(batch: Batch, out):
+    if out is None:
+        out = torch.empty(batch.num_graphs, dtype=torch.int64, device=batch.offsets.device)
+    _require_cuda(out, "out", (torch.int64,))
+    if out.numel() < batch.num_graphs:
+        raise ValueError("out must have num_graphs entries")
+    return out
+
+
+def kc_count_batched(dag: Dag, batch: Batch, params=None, out: torch.Tensor | None = None, stream=None):
+    """(sum, out) with out[g] = graph g's ks[g]-clique count (int64 storage of uint64)."""
+    out = _totals(batch, out)
+    t = ctypes.c_uint64()
+    _check(_load().kc_count_batched(dag.handle, batch.ref, _params(params), out.data_ptr(), ctypes.byref(t),
+                                    _stream(stream)))
+    return int(t.value), out[:batch.num_graphs]
+
+
+class Plan:
+    """kc_plan: a prepared batched pass; launch() only enqueues (capturable)."""
+
+    def __init__(self, dag: Dag, batch: Batch, params=None, out: torch.Tensor | None = None, stream=None):
+        self.dag, self.batch = dag, batch  # keep the buffers alive
+        self.out = _totals(batch, out)
+        h = ctypes.c_void_p()
+        _check(_load().kc_plan_create(dag.handle, batch.ref, _params(params), self.out.data_ptr(),
+                                      ctypes.byref(h), _stream(stream)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_load().kc_plan_launch(self._h, _stream(stream)))
+
+    def result(self, stream=None) -> int:
+        t = ctypes.c_uint64()
+        _check(_load().kc_plan_result(self._h, ctypes.byref(t), _stream(stream)))
+        return int(t.value)
+
+    def free(self):
+        if self._h and self._h.value:
+            _load().kc_plan_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def kc_autotune_batched(dag: Dag, batch: Batch, out: torch.Tensor | None = None, stream=None):
+    """(params dict, best ms per launch) of the fastest tunables for this batch."""
+    out = _totals(batch, out)
+    p, ms = _Params(), ctypes.c_float()
+    _check(_load().kc_autotune_batched(dag.handle, batch.ref, out.data_ptr(), ctypes.byref(p), ctypes.byref(ms),
+                                       _stream(stream)))
+    return {"light_max": int(p.light_max), "compact_max": int(p.compact_max), "chunk": int(p.chunk)}, float(ms.value)
+
+
 def kc_dag_get_stats(dag: Dag, stream=None) -> dict:
     st = _Stats()
     _check(_load().kc_dag_get_stats(dag.handle, ctypes.byref(st), _stream(stream)))
@@ -232,11 +335,13 @@ def kc_kernel_launches() -> int:
     return int(_load().kc_kernel_launches())
 
 
-# short forms of the spec interface
+# short forms of the paper's interface (Algorithm 1: Orient, arb-count)
 orient = kc_orient
 count = kc_count
 count_per_vertex = kc_count_per_vertex
 count_per_arc = kc_count_per_arc
+count_batched = kc_count_batched
+autotune_batched = kc_autotune_batched
 dag_stats = kc_dag_get_stats
 
 

@@ -1,0 +1,44 @@
+"""Host-side logic without a GPU: the batch recipe and the CSR concatenation
+that builds a batch's union graph."""
+import numpy as np
+
+import oracle
+from paper_2002_10047_gb300 import graphgen as gg
+
+
+def test_concat_csr_equals_disjoint_union():
+    specs = gg.batch_specs(40, seed=3, n_hi=600)
+    graphs = gg.build_batch(specs) + [gg.empty(0), gg.complete(7), gg.empty(2)]
+    u, off = gg.concat_csr(graphs)
+    ref = gg.disjoint_union(graphs)
+    assert u.n == ref.n == int(off[-1])
+    assert u.row_ptr.dtype == np.uint64 and u.col.dtype == np.uint32
+    assert np.array_equal(u.row_ptr, ref.row_ptr) and np.array_equal(u.col, ref.col)
+    assert np.array_equal(np.diff(off.astype(np.int64)), [g.n for g in graphs])
+
+
+def test_union_counts_are_per_graph_sums():
+    """Counting the union graph g by g (roots restricted to each vertex range)
+    gives each graph's own count: the property the batched pass relies on."""
+    specs = gg.batch_specs(12, seed=5, n_hi=400)
+    graphs = gg.build_batch(specs)
+    u, off = gg.concat_csr(graphs)
+    for k in (3, 4, 5):
+        dag = oracle.orient(u, "degree")
+        total = 0
+        for i, g in enumerate(graphs):
+            want = oracle.count(oracle.orient(g, "degree"), k)
+            # the union's roots in graph i's id range (its out-lists stay inside it)
+            assert oracle.count(dag, k, lo=int(off[i]), hi=int(off[i + 1])) == want
+            total += want
+        assert oracle.count(dag, k) == total
+
+
+def test_batch_recipe_ranges():
+    specs = gg.batch_specs(4096, seed=3)
+    kinds = [s.kind for s in specs]
+    assert 1900 < kinds.count("er") < 2200
+    assert min(s.n for s in specs) >= 50 and max(s.n for s in specs) <= 20000
+    assert min(s.avg_deg for s in specs) >= 4 and max(s.avg_deg for s in specs) <= 64
+    assert {s.k for s in specs} == set(range(3, 9))
+    assert gg.batch_specs(8, seed=3) == specs[:8]  # counter-based: a prefix is stable
