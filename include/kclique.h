@@ -206,14 +206,23 @@ typedef struct {
  *   compact_max  bitset width of the compacted sub-problems: candidate sets
  *                of at most this many vertices are renumbered into a 1- or
  *                2-word (64- or 128-bit) bit matrix (1 .. 128; default 128)
- *   chunk        roots a warp takes per pull from the atomic work queue of
- *                the warp kernel (default 1)
+ *   chunk        work a warp takes per pull from the atomic work queue of
+ *                the warp kernel: roots (out-degree order) or groups of 32
+ *                vertex ids (id order) (default 1)
+ *   light_order  order in which warps take the warp roots:
+ *                KC_LIGHT_BY_DEGREE = decreasing out-degree (load balance),
+ *                KC_LIGHT_BY_ID = increasing vertex id (locality: a batch's
+ *                graphs are counted one id range at a time, so their
+ *                out-lists stay in L2); 0 = id order for batches
  * Every setting gives the same counts; only the speed differs.
  */
+#define KC_LIGHT_BY_DEGREE 1
+#define KC_LIGHT_BY_ID 2
 typedef struct {
   uint32_t light_max;
   uint32_t compact_max;
   uint32_t chunk;
+  uint32_t light_order;
 } kc_params;
 
 /*
@@ -249,7 +258,7 @@ kc_status kc_plan_result(kc_plan *p, uint64_t *h_total, kc_stream_t stream);
 void kc_plan_free(kc_plan *p);
 
 /*
- * kc_autotune_batched -- the tunables (light_max, compact_max, chunk) that
+ * kc_autotune_batched -- the tunables (light_order, light_max, compact_max, chunk) that
  * count the batch fastest on this device: times each candidate of a small
  * grid (two launches each, CUDA events, after one warm-up launch) and writes
  * the fastest to *out; *h_best_ms (optional) receives its time. d_totals is

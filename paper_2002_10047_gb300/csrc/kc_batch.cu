@@ -2,7 +2,8 @@
 // disjoint union of many graphs, each root counting its own graph's k and
 // adding into its graph's total (include/kclique.h, "Batches"). A prepared
 // plan makes the pass capturable into a CUDA graph; the autotuner picks the
-// warp/block threshold, the compacted bitset width and the queue chunk.
+// warp-root order, the warp/block threshold, the compacted bitset width and
+// the queue chunk.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -13,7 +14,6 @@
 
 struct kc_plan {
   kc::LaunchPlan P;
-  bool pv = false;
   uint32_t num_graphs = 0;
   uint64_t *totals = nullptr;  // caller's d_totals
   void *work = nullptr;        // owned: total, status, queues
@@ -26,7 +26,8 @@ namespace {
 kc_status check_batch(const kc_dag *d, const kc_batch *b, const kc_params *prm) {
   if (!d || !b || b->num_graphs == 0 || !b->d_vertex_offsets || !b->d_k) return KC_EINVAL;
   if (b->k_min < 3 || b->k_min > KC_KMAX) return KC_EINVAL;
-  if (prm && (prm->light_max > (uint32_t)kc::kLightMax || prm->compact_max > (uint32_t)kc::kCompactMax))
+  if (prm && (prm->light_max > (uint32_t)kc::kLightMax || prm->compact_max > (uint32_t)kc::kCompactMax ||
+              prm->light_order > KC_LIGHT_BY_ID))
     return KC_EINVAL;
   if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
   return KC_OK;
@@ -46,7 +47,7 @@ kc_status kc_plan_create(const kc_dag *d, const kc_batch *b, const kc_params *pr
   p->num_graphs = b->num_graphs;
   p->totals = d_totals;
   p->stream = s;
-  cudaError_t e = kc::plan_count(d, b->k_min, false, false, prm, &p->P);
+  cudaError_t e = kc::plan_count(d, b->k_min, false, false, prm, true, &p->P);
   if (e == cudaSuccess) e = cudaMallocAsync(&p->work, kc::kc_work_bytes(), s);
   if (e == cudaSuccess && p->P.scratch_bytes) e = cudaMallocAsync(&p->scratch, p->P.scratch_bytes, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->work, 0, kc::kc_work_bytes(), s);
@@ -112,6 +113,7 @@ kc_status kc_autotune_batched(const kc_dag *d, const kc_batch *b, uint64_t *d_to
   const kc_status c = check_batch(d, b, nullptr);
   if (c != KC_OK) return c;
   cudaStream_t s = (cudaStream_t)stream;
+  static const uint32_t kOrder[] = {KC_LIGHT_BY_ID, KC_LIGHT_BY_DEGREE};
   static const uint32_t kLight[] = {32, 48, 64};
   static const uint32_t kCompact[] = {64, 128};
   static const uint32_t kChunk[] = {1, 4, 16};
@@ -119,32 +121,33 @@ kc_status kc_autotune_batched(const kc_dag *d, const kc_batch *b, uint64_t *d_to
   KC_CK(cudaEventCreate(&e0));
   KC_CK(cudaEventCreate(&e1));
   float best = -1.f;
-  kc_params best_p = {0, 0, 0};
+  kc_params best_p = {0, 0, 0, 0};
   kc_status st = KC_OK;
-  for (uint32_t lm : kLight)
-    for (uint32_t cm : kCompact)
-      for (uint32_t ch : kChunk) {
-        if (st != KC_OK) break;
-        const kc_params prm = {lm, cm, ch};
-        kc_plan *p = nullptr;
-        st = kc_plan_create(d, b, &prm, d_totals, &p, stream);
-        if (st != KC_OK) break;
-        st = kc_plan_launch(p, stream);  // warm-up
-        if (st == KC_OK) st = kc_plan_result(p, nullptr, stream);
-        float ms = 0.f;
-        if (st == KC_OK) {
-          cudaEventRecord(e0, s);
-          for (int r = 0; r < 2 && st == KC_OK; ++r) st = kc_plan_launch(p, stream);
-          cudaEventRecord(e1, s);
+  for (uint32_t lo : kOrder)
+    for (uint32_t lm : kLight)
+      for (uint32_t cm : kCompact)
+        for (uint32_t ch : kChunk) {
+          if (st != KC_OK) break;
+          const kc_params prm = {lm, cm, ch, lo};
+          kc_plan *p = nullptr;
+          st = kc_plan_create(d, b, &prm, d_totals, &p, stream);
+          if (st != KC_OK) break;
+          st = kc_plan_launch(p, stream);  // warm-up
           if (st == KC_OK) st = kc_plan_result(p, nullptr, stream);
-          if (st == KC_OK) cudaEventElapsedTime(&ms, e0, e1);
+          float ms = 0.f;
+          if (st == KC_OK) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 2 && st == KC_OK; ++r) st = kc_plan_launch(p, stream);
+            cudaEventRecord(e1, s);
+            if (st == KC_OK) st = kc_plan_result(p, nullptr, stream);
+            if (st == KC_OK) cudaEventElapsedTime(&ms, e0, e1);
+          }
+          kc_plan_free(p);
+          if (st == KC_OK && (best < 0.f || ms < best)) {
+            best = ms;
+            best_p = prm;
+          }
         }
-        kc_plan_free(p);
-        if (st == KC_OK && (best < 0.f || ms < best)) {
-          best = ms;
-          best_p = prm;
-        }
-      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != KC_OK) return st;

@@ -1169,8 +1169,37 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
   unsigned ovf = 0;
   unsigned long long tsum = 0;
   uint8_t *slot = smem + (size_t)warp * light_layout(PV, PA).bytes;
-  const uint32_t nlight = a.n_light_end - a.n_big;
   const uint32_t chunk = a.chunk ? a.chunk : 1u;
+  if (a.light_by_id) {
+    // Roots in vertex-id order, so that a batch's graphs are counted one
+    // region at a time and their out-lists stay in L2: each pull takes
+    // 32*chunk ids, lanes test 32 of them at once, the warp counts the
+    // qualifying ones (light_min <= d+ <= light_max) in id order.
+    for (;;) {
+      unsigned idx = 0;
+      if (lane == 0) idx = past_deadline(a) ? 0xffffffffu : atomicAdd(&a.queue[2], chunk);
+      idx = __shfl_sync(0xffffffffu, idx, 0);
+      if (idx == 0xffffffffu || (unsigned long long)idx * 32ull >= a.n) break;
+      const uint32_t lo = idx * 32u, hi = (uint32_t)min((unsigned long long)a.n, (unsigned long long)(idx + chunk) * 32ull);
+      for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t u = base + lane;
+        bool ok = false;
+        if (u < hi) {
+          const uint32_t d = (uint32_t)(a.ptr[u + 1] - a.ptr[u]);
+          ok = d >= a.light_min && d <= a.light_max;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, ok);
+        while (mask) {
+          const int l = __ffs(mask) - 1;
+          mask &= mask - 1;
+          warp_root<PV, PA>(a, base + (uint32_t)l, slot, tsum, ovf, &w_next[warp]);
+        }
+      }
+    }
+    finish_block(a, tsum, ovf, red, kWarps);
+    return;
+  }
+  const uint32_t nlight = a.n_light_end - a.n_big;
   for (;;) {
     unsigned idx = 0;
     if (lane == 0) idx = past_deadline(a) ? 0xffffffffu : atomicAdd(&a.queue[2], chunk);

@@ -131,6 +131,12 @@ struct CountArgs {
   // (<= kCompactMax), roots a warp takes per queue pull in the warp-root kernel
   uint32_t compact_max;
   uint32_t chunk;
+  // warp roots in vertex-id order instead of the order array: the roots
+  // u < n with light_min <= d+(u) <= light_max (queue[2] counts pulls of
+  // 32*chunk ids)
+  uint32_t light_by_id;
+  uint32_t n;
+  uint32_t light_min, light_max;
 };
 
 // A configured counting pass (kc_api.cu).

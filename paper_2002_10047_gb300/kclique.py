@@ -25,6 +25,8 @@ KC_KMAX = 32
 KC_ORIENT_DEGREE = 0
 KC_ORIENT_GP = 1
 KC_VALIDATE_SYMMETRY = 0x100
+KC_LIGHT_BY_DEGREE = 1
+KC_LIGHT_BY_ID = 2
 _METHODS = {"degree": KC_ORIENT_DEGREE, "gp": KC_ORIENT_GP}
 
 
@@ -53,7 +55,8 @@ class _Batch(ctypes.Structure):
 
 
 class _Params(ctypes.Structure):
-    _fields_ = [("light_max", ctypes.c_uint32), ("compact_max", ctypes.c_uint32), ("chunk", ctypes.c_uint32)]
+    _fields_ = [("light_max", ctypes.c_uint32), ("compact_max", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("light_order", ctypes.c_uint32)]
 
 
 class _Stats(ctypes.Structure):
@@ -254,7 +257,8 @@ def _params(params):
     if params is None:
         return None
     if isinstance(params, dict):
-        params = (params.get("light_max", 0), params.get("compact_max", 0), params.get("chunk", 0))
+        params = (params.get("light_max", 0), params.get("compact_max", 0), params.get("chunk", 0),
+                  params.get("light_order", 0))
     return ctypes.byref(_Params(*[int(x) for x in params]))
 
 
@@ -313,7 +317,8 @@ def kc_autotune_batched(dag: Dag, batch: Batch, out: torch.Tensor | None = None,
     p, ms = _Params(), ctypes.c_float()
     _check(_load().kc_autotune_batched(dag.handle, batch.ref, out.data_ptr(), ctypes.byref(p), ctypes.byref(ms),
                                        _stream(stream)))
-    return {"light_max": int(p.light_max), "compact_max": int(p.compact_max), "chunk": int(p.chunk)}, float(ms.value)
+    return ({"light_max": int(p.light_max), "compact_max": int(p.compact_max), "chunk": int(p.chunk),
+             "light_order": int(p.light_order)}, float(ms.value))
 
 
 def kc_dag_get_stats(dag: Dag, stream=None) -> dict:

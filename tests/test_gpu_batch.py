@@ -85,7 +85,8 @@ def test_batch_matches_one_call_per_graph(kc, small_batch):
 
 
 @pytest.mark.parametrize("params", [
-    (2, 1, 1), (32, 64, 4), (64, 128, 16), (17, 100, 7), (48, 0, 0), (0, 64, 0), (0, 0, 32),
+    (2, 1, 1, 2), (32, 64, 4, 1), (64, 128, 16, 2), (17, 100, 7, 1), (48, 0, 0, 0), (0, 64, 0, 2),
+    (0, 0, 32, 1), (3, 128, 1, 2), (64, 64, 100, 2),
 ])
 def test_batch_params_give_same_counts(kc, small_batch, params):
     graphs, ks, want = small_batch
@@ -105,7 +106,7 @@ def test_batch_params_single_graph_all_root_classes(kc):
     for k in range(3, 8):
         want = oracle.count(od, k, threads=8)
         b = kc.Batch(offs, torch.tensor([k], dtype=torch.uint8, device="cuda"))
-        for params in ((2, 1, 1), (32, 64, 16), (64, 128, 4)):
+        for params in ((2, 1, 1, 1), (32, 64, 16, 2), (64, 128, 4, 1), (64, 128, 1, 2), (0, 0, 0, 0)):
             tot, out = kc.count_batched(dag, b, params=params)
             assert tot == want and int(kc.as_uint64(out)[0]) == want, (k, params)
 
@@ -113,7 +114,7 @@ def test_batch_params_single_graph_all_root_classes(kc):
 def test_batch_plan_graph_capture_replay(kc, small_batch):
     graphs, ks, want = small_batch
     dag, b = device_batch(kc, graphs, ks)
-    plan = kc.Plan(dag, b, params=(32, 128, 4))
+    plan = kc.Plan(dag, b, params=(32, 128, 4, 2))
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(side):  # one eager launch before capture
@@ -136,7 +137,7 @@ def test_batch_autotune(kc, small_batch):
     dag, b = device_batch(kc, graphs, ks)
     params, ms = kc.autotune_batched(dag, b)
     assert params["light_max"] in (32, 48, 64) and params["compact_max"] in (64, 128)
-    assert params["chunk"] in (1, 4, 16) and ms > 0
+    assert params["chunk"] in (1, 4, 16) and params["light_order"] in (1, 2) and ms > 0
     _, out = kc.count_batched(dag, b, params=params)
     assert np.array_equal(kc.as_uint64(out), want)
 
@@ -174,7 +175,8 @@ def test_batch_full_4096_bit_exact(kc):
     want = oracle_totals(graphs, ks)
     dag, b = device_batch(kc, graphs, ks)
     del graphs
-    tot, out = kc.count_batched(dag, b)
-    got = kc.as_uint64(out)
-    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
-    assert tot == int(want.sum())
+    for params in (None, (0, 0, 0, kc.KC_LIGHT_BY_DEGREE)):
+        tot, out = kc.count_batched(dag, b, params=params)
+        got = kc.as_uint64(out)
+        assert np.array_equal(got, want), (params, np.nonzero(got != want)[0][:10])
+        assert tot == int(want.sum())
