@@ -48,8 +48,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--json-out", default=None)
-    ap.add_argument("--workload", choices=["rmat", "batch"], default="rmat",
-                    help="rmat: one large graph, k = --ks; batch: the 4096-graph mixed batch")
+    ap.add_argument("--workload", choices=["rmat", "batch", "serve"], default="rmat",
+                    help="rmat: one large graph, k = --ks; batch: the 4096-graph mixed batch; "
+                         "serve: Poisson request stream on a pool of resident graphs")
+    ap.add_argument("--rates", default="100,300,1000,3000", help="serve: arrival rates swept (req/s)")
+    ap.add_argument("--requests", type=int, default=400, help="serve: requests per rate")
+    ap.add_argument("--pool-max-scale", type=int, default=14)
+    ap.add_argument("--pool-max-ef", type=int, default=16)
+    ap.add_argument("--pool-max-er", type=int, default=200000)
+    ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--grid-share", type=int, default=25, help="serve: percent of the full grid per request")
+    ap.add_argument("--request-timeout-ms", type=int, default=1000)
     ap.add_argument("--batch-graphs", type=int, default=4096)
     return ap.parse_args()
 
@@ -672,18 +681,234 @@ def run_batch(args, rank, world):
             f.write(out + "\n")
 
 
+# ------------------------------------------------------------- serving workload
+SERVE_METRIC = "served requests/s at p99 latency"
+SERVE_UNIT = "req/s"
+
+
+def serve_workload(args) -> str:
+    return (f"pool of 200 resident graphs, seed 5: 100 R-MAT (scale U{{10..{args.pool_max_scale}}}, edge factor "
+            f"U{{8..{args.pool_max_ef}}}) and 100 Erdos-Renyi (n U[1000,{args.pool_max_er}], average degree U[4,64]); Poisson "
+            f"arrivals at {args.rates} req/s, {args.requests} requests per rate; k U{{3..9}}, count or "
+            "per-vertex count 50/50; admission by device-memory footprint")
+
+
+def make_pool(args):
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_2002_10047_gb300 import graphgen as gg
+    key = 5
+    sc = gg.uniform_ints(key, 31, 100, 10, args.pool_max_scale)
+    ef = gg.uniform_ints(key, 32, 100, 8, args.pool_max_ef)
+    ern = gg.uniform_ints(key, 33, 100, 1000, args.pool_max_er)
+    erd = gg.uniform_ints(key, 34, 100, 4, 64)
+
+    def mk(i):
+        if i < 100:
+            return gg.rmat(int(sc[i]), int(ef[i]), seed=1000 + i, permute=True)
+        j = i - 100
+        n = int(ern[j])
+        return gg.erdos_renyi(n, min(1.0, float(erd[j]) / max(1, n - 1)), 2000 + j)
+
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        return list(ex.map(mk, range(200)))
+
+
+def serve_requests(count: int, rate: float, seed: int):
+    """(arrival offsets s, graph index, k, per_vertex) of a Poisson stream."""
+    from paper_2002_10047_gb300 import graphgen as gg
+    u = np.array([gg._rnd_unit(gg._stream_key(seed, 41), i) for i in range(count)])
+    gaps = -np.log1p(-u) / rate
+    t = np.cumsum(gaps) - gaps[0]
+    gi = gg.uniform_ints(seed, 42, count, 0, 199)
+    ks = gg.uniform_ints(seed, 43, count, 3, 9)
+    pv = gg.uniform_ints(seed, 44, count, 0, 1)
+    return t, gi, ks, pv
+
+
+def oracle_serve_rate(pool, seconds: float, threads: int):
+    """Oracle requests (orient + count or per-vertex count) of the seed-5 stream, in
+    stream order, requests in parallel on the host cores, until the budget is spent."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    _, gi, ks, pv = serve_requests(4096, 1.0, 5)
+
+    def one(i):
+        dag = oracle.orient(pool[gi[i]], "degree")
+        if pv[i]:
+            return oracle.count_per_vertex(dag, int(ks[i]))[0]
+        return oracle.count(dag, int(ks[i]))
+
+    done, t0, step = 0, time.perf_counter(), threads
+    with ThreadPoolExecutor(threads) as ex:
+        while done < len(gi) and time.perf_counter() - t0 < seconds:
+            hi = min(len(gi), done + step)
+            list(ex.map(one, range(done, hi)))
+            done = hi
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+def run_reference_serve(args, rank, world):
+    if rank != 0:
+        return
+    pool = make_pool(args)
+    cores = host_cores()
+    budget = max(2.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    rates, desc = [], ""
+    for i in range(args.warmup + args.steps):
+        r, done, dt = oracle_serve_rate(pool, budget, cores)
+        desc = f"the first {done} requests of the seed-5 stream in {dt:.1f} s (no arrival process)"
+        if i >= args.warmup:
+            rates.append(r)
+    v = statistics.median(rates)
+    line = {"impl": "reference", "metric": SERVE_METRIC, "value": v, "unit": SERVE_UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": serve_workload(args)},
+            "cpu_baseline": {"value": v, "unit": SERVE_UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {desc}"},
+            "e2e": {"value": v, "unit": SERVE_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _drive(kc, srv, dags, ns, reqs, timeout_us):
+    """Submit a Poisson stream at its arrival times and collect every result."""
+    import queue as _q
+
+    import torch
+    t_arr, gi, ks, pv = reqs
+    ids = _q.Queue()
+    res = [None] * len(t_arr)
+    host_pv = {}
+
+    def collector():
+        for _ in range(len(t_arr)):
+            i, rid = ids.get()
+            r = srv.wait(rid)
+            if pv[i]:
+                g = int(gi[i])
+                buf = host_pv.get(g)
+                if buf is None:
+                    buf = host_pv[g] = torch.empty(max(ns[g], 1), dtype=torch.int64).pin_memory()
+                srv.fetch_per_vertex(rid, buf[:ns[g]])
+                srv.release(rid)
+            else:
+                srv.forget(rid)
+            r["done_at"] = time.perf_counter()
+            res[i] = r
+
+    th = threading.Thread(target=collector)
+    th.start()
+    t0 = time.perf_counter()
+    for i in range(len(t_arr)):
+        while True:
+            dt = t0 + t_arr[i] - time.perf_counter()
+            if dt <= 0:
+                break
+            if dt > 2e-4:
+                time.sleep(dt - 1e-4)
+        rid = srv.submit(dags[int(gi[i])], int(ks[i]), per_vertex=bool(pv[i]), timeout_us=timeout_us)
+        ids.put((i, rid))
+    th.join()
+    t_end = max(r["done_at"] for r in res)
+    return res, t_end - t0
+
+
+def run_serve(args, rank, world):
+    import torch
+
+    from paper_2002_10047_gb300 import build as kbuild
+    kbuild.build()
+    from paper_2002_10047_gb300 import kclique as kc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    pool = make_pool(args)
+    dags, ns = [], []
+    for g in pool:
+        rp, col = kc.csr_to_device(g)
+        dags.append(kc.orient(rp, col, g.n, method="degree"))
+        ns.append(g.n)
+    torch.cuda.synchronize()
+    resident = sum(g.row_ptr.nbytes + g.col.nbytes // 2 for g in pool)
+    rates = [float(x) for x in args.rates.split(",")]
+    timeout_us = args.request_timeout_ms * 1000
+    budget = 8 << 30
+    sweep = {"continuous": [], "one_at_a_time": []}
+    all_ok = True
+    with ClockSampler(local) as clk:
+        for mode, slots, share in (("continuous", args.slots, args.grid_share), ("one_at_a_time", 1, 100)):
+            srv = kc.Server(slots=slots, hbm_budget=budget, grid_share_pct=share)
+            try:
+                warm = serve_requests(64, 1e5, 99)
+                _drive(kc, srv, dags, ns, warm, timeout_us)
+                for rate in rates:
+                    reqs = serve_requests(args.requests, rate, 5)
+                    res, span = _drive(kc, srv, dags, ns, reqs, timeout_us)
+                    lat = np.array([r["latency_s"] for r in res]) * 1e3
+                    ok = [r["status"] == kc.KC_OK for r in res]
+                    tmo = sum(r["status"] == kc.KC_ETIMEDOUT for r in res)
+                    hist = {}
+                    for r in res:
+                        hist[str(r["status"])] = hist.get(str(r["status"]), 0) + 1
+                    all_ok &= all(r["status"] in (kc.KC_OK, kc.KC_ETIMEDOUT) for r in res)
+                    st = srv.stats()
+                    sweep[mode].append({
+                        "rate": rate, "requests": len(res), "completed_ok": int(sum(ok)), "timed_out": int(tmo),
+                        "throughput": len(res) / span, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                        "peak_in_flight": st["peak_in_flight"], "peak_bytes": st["peak_bytes"],
+                        "statuses": hist})
+                    if mode == "continuous" and rate == rates[-1]:
+                        last = (reqs, res)
+            finally:
+                srv.close()
+    # every served total equals the same request run alone (sampled)
+    reqs, res = last
+    _, gi, ks, pv = reqs
+    idx = np.linspace(0, len(res) - 1, min(60, len(res))).astype(int)
+    mism = 0
+    for i in idx:
+        if res[i]["status"] == kc.KC_OK:
+            mism += int(kc.count(dags[int(gi[i])], int(ks[i])) != res[i]["total"])
+    if rank != 0:
+        return
+    top = sweep["continuous"][-1]
+    line = {
+        "metric": SERVE_METRIC, "value": top["throughput"], "unit": SERVE_UNIT, "n_gpus": world,
+        "steps": len(rates), "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": serve_workload(args), "slots": args.slots, "grid_share_pct": args.grid_share,
+                   "hbm_budget": budget,
+                   "request_timeout_us": timeout_us, "resident_csr_bytes": int(resident),
+                   "latency": "host clock, submission at the arrival time to completion"},
+        "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"], "sweep": sweep,
+        "p99_speedup_vs_one_at_a_time": (sweep["one_at_a_time"][-1]["p99_ms"] / top["p99_ms"]),
+        "alone_check": {"sampled": int(len(idx)), "mismatches": mism}, "statuses_ok": bool(all_ok),
+        "clocks": clk.summary(),
+    }
+    out = json.dumps(line)
+    print(out, flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(out + "\n")
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
-        (run_reference_batch if args.workload == "batch" else run_reference)(args, rank, world)
+        {"batch": run_reference_batch, "serve": run_reference_serve}.get(args.workload, run_reference)(
+            args, rank, world)
         return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        (run_batch if args.workload == "batch" else run_ours)(args, rank, world)
+        {"batch": run_batch, "serve": run_serve}.get(args.workload, run_ours)(args, rank, world)
     finally:
         if world > 1:
             import torch.distributed as dist

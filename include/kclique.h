@@ -268,6 +268,68 @@ kc_status kc_autotune_batched(const kc_dag *d, const kc_batch *b, uint64_t *d_to
                               float *h_best_ms, kc_stream_t stream);
 
 /*
+ * Serving: a request loop for count and per-vertex count requests on
+ * device-resident oriented graphs (the paper counts one graph per call; this
+ * is the many-request form of the same pass).
+ *
+ * kc_server_create starts a dispatcher thread with cfg->slots slots (one
+ * CUDA stream each) on the current device. kc_server_submit queues a request
+ * (a kc_dag that stays valid until the request is released, k in
+ * [3, KC_KMAX], per_vertex 0 or 1, timeout_us the time budget from submission
+ * or 0 for none) and returns at once. Requests are admitted
+ * first come, first served, as soon as a slot is free and their device
+ * footprint (the per-vertex output 8n bytes, the work block and the global
+ * scratch of their largest roots) fits cfg->hbm_budget beside the requests in
+ * flight; a request that does not fit waits, unless nothing else is
+ * running (so a client holding per-vertex outputs cannot stall the queue). Admitted requests run concurrently on their slots' streams, each
+ * with grids sized to its own work and capped at cfg->grid_share_pct percent
+ * of the full persistent grid, so their kernels overlap on the GPU. The result of a
+ * request does not depend on what else is in flight. A request whose time
+ * budget runs out stops taking new roots (the kernels check the device clock,
+ * mapped from the host clock when the server starts) and completes with
+ * status KC_ETIMEDOUT; roots already taken finish first.
+ *
+ * kc_server_wait blocks until request id completes (timeout_ms < 0: no limit;
+ * KC_ETIMEDOUT if it has not completed in time) and fills *out: out->status
+ * is the request's own kc_status, out->total its count, and the times are
+ * host steady-clock nanoseconds from submission. A count request is released
+ * by a successful wait; a per-vertex request keeps its output (and its share
+ * of the budget) until kc_server_release, after kc_server_fetch_per_vertex
+ * has copied the n counts to dst (host or device memory; synchronises
+ * `stream`). kc_server_destroy waits for the requests in flight and drops
+ * the queued ones.
+ */
+typedef struct kc_server kc_server;
+typedef struct {
+  uint32_t slots;          /* requests in flight at most, 1 .. 64 */
+  uint32_t grid_share_pct; /* grid cap per request, percent of the full persistent grid (0 = 100) */
+  uint64_t hbm_budget;     /* bytes of request memory in flight */
+} kc_server_config;
+typedef struct {
+  int status;          /* the request's kc_status */
+  int slot;            /* slot it ran on */
+  uint64_t total;      /* its count */
+  uint64_t queue_ns;   /* submission to admission */
+  uint64_t run_ns;     /* admission to completion */
+  uint64_t latency_ns; /* submission to completion */
+} kc_request_result;
+typedef struct {
+  uint64_t submitted, admitted, completed;
+  uint64_t peak_in_flight; /* most requests on the GPU at once */
+  uint64_t peak_bytes;     /* most request memory admitted at once */
+  uint64_t bytes_in_use;   /* request memory held now */
+  uint64_t queued;         /* requests waiting now */
+} kc_server_stats;
+kc_status kc_server_create(const kc_server_config *cfg, kc_server **out);
+kc_status kc_server_submit(kc_server *s, const kc_dag *d, int k, int per_vertex, uint64_t timeout_us,
+                           uint64_t *req_id);
+kc_status kc_server_wait(kc_server *s, uint64_t req_id, int timeout_ms, kc_request_result *out);
+kc_status kc_server_fetch_per_vertex(kc_server *s, uint64_t req_id, uint64_t *dst, kc_stream_t stream);
+kc_status kc_server_release(kc_server *s, uint64_t req_id);
+kc_status kc_server_get_stats(kc_server *s, kc_server_stats *out);
+void kc_server_destroy(kc_server *s);
+
+/*
  * Work statistics of an oriented graph, used for the bytes a counting pass
  * must move (computed exactly on the device):
  *   sum_out_sq     sum over roots u of d+(u)^2

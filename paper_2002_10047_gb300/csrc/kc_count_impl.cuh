@@ -37,6 +37,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "kc_internal.cuh"
 
 namespace kc {
@@ -472,6 +474,18 @@ __device__ __forceinline__ uint32_t slot_select(const Slot sl, uint32_t W, uint3
   return lo * 64 + (uint32_t)(__ffsll((long long)bb) - 1);
 }
 
+// Per-lane deadline check before a first-level subproblem of a block root
+// (served passes with a time budget): past it, the subproblem is skipped and
+// the pass reports ST_TIMEOUT.
+__device__ __forceinline__ bool lane_past(uint64_t dl_ns, unsigned *dl_status) {
+  if (dl_ns == 0) return false;
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  if (t <= dl_ns) return false;
+  atomicOr(dl_status, ST_TIMEOUT);
+  return true;
+}
+
 // Cliques taking `picks` (>= 2) more vertices from the slot's set of
 // s <= kCompactMax root positions: the set is compacted to local ids 0..s-1
 // (rank order is kept), its induced symmetric rows are extracted from the
@@ -479,7 +493,8 @@ __device__ __forceinline__ uint32_t slot_select(const Slot sl, uint32_t W, uint3
 // picked vertices go to the root counters rc. Returns the warp-uniform total.
 template <bool PV>
 __device__ unsigned long long compact_count(const MatView M, uint32_t s, int picks, const Slot sl,
-                                            unsigned long long *rc, unsigned &ovf_out) {
+                                            unsigned long long *rc, unsigned &ovf_out, uint64_t dl_ns = 0,
+                                            unsigned *dl_status = nullptr) {
   unsigned ovf = 0;
   const unsigned lane = lane_id();
   const uint32_t W = M.W;
@@ -527,12 +542,12 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
       uint64_t C[1] = {sl.S[q] & above_word(q, 0)};
       const int pc = __popcll(C[0]);
       if (picks == 2) sub = (unsigned long long)pc;
-      else if (pc >= picks - 1) sub = dfs<1, 1, PV>(C, picks - 1, V, 0, ovf);
+      else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, 1, PV>(C, picks - 1, V, 0, ovf);
     } else {
       uint64_t C[2] = {sl.S[2 * q] & above_word(q, 0), sl.S[2 * q + 1] & above_word(q, 1)};
       const int pc = __popcll(C[0]) + __popcll(C[1]);
       if (picks == 2) sub = (unsigned long long)pc;
-      else if (pc >= picks - 1) sub = dfs<1, 2, PV>(C, picks - 1, V, 0, ovf);
+      else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, 2, PV>(C, picks - 1, V, 0, ovf);
     }
     if (PV && picks > 2 && sub) atomic_add_ck(&sl.cs[q], sub, ovf);
     acc = add_ck(acc, sub, ovf);
@@ -557,7 +572,8 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
 // words) and each lane runs the recursion on the root matrix with NW-word sets
 // in registers. Returns the warp-uniform total.
 template <int NW, bool PV>
-__device__ unsigned long long split_count(const MatView M, uint32_t s, int picks, const Slot sl, unsigned &ovf_out) {
+__device__ unsigned long long split_count(const MatView M, uint32_t s, int picks, const Slot sl, unsigned &ovf_out,
+                                          uint64_t dl_ns = 0, unsigned *dl_status = nullptr) {
   unsigned ovf = 0;
   const unsigned lane = lane_id();
   const uint32_t W = M.W;
@@ -574,7 +590,7 @@ __device__ unsigned long long split_count(const MatView M, uint32_t s, int picks
     }
     unsigned long long sub = 0;
     if (picks == 2) sub = (unsigned long long)pc;
-    else if (pc >= picks - 1) sub = dfs<1, NW, PV>(C, picks - 1, M, 0, ovf);
+    else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, NW, PV>(C, picks - 1, M, 0, ovf);
     if (PV && picks > 2 && sub) atomic_add_ck(&M.cnt[x], sub, ovf);
     acc = add_ck(acc, sub, ovf);
   }
@@ -639,11 +655,12 @@ __device__ unsigned long long wide_count(const MatView M, int picks, const Slot 
 }
 
 template <bool PV>
-__device__ unsigned long long split_dispatch(const MatView M, uint32_t s, int picks, const Slot sl, unsigned &ovf) {
-  if (M.W <= 2) return split_count<2, PV>(M, s, picks, sl, ovf);
-  if (M.W <= 4) return split_count<4, PV>(M, s, picks, sl, ovf);
-  if (M.W <= 8) return split_count<8, PV>(M, s, picks, sl, ovf);
-  if (M.W <= 12) return split_count<12, PV>(M, s, picks, sl, ovf);
+__device__ unsigned long long split_dispatch(const MatView M, uint32_t s, int picks, const Slot sl, unsigned &ovf,
+                                             uint64_t dl_ns = 0, unsigned *dl_status = nullptr) {
+  if (M.W <= 2) return split_count<2, PV>(M, s, picks, sl, ovf, dl_ns, dl_status);
+  if (M.W <= 4) return split_count<4, PV>(M, s, picks, sl, ovf, dl_ns, dl_status);
+  if (M.W <= 8) return split_count<8, PV>(M, s, picks, sl, ovf, dl_ns, dl_status);
+  if (M.W <= 12) return split_count<12, PV>(M, s, picks, sl, ovf, dl_ns, dl_status);
   return wide_count<PV>(M, picks, sl, ovf);
 }
 
@@ -668,6 +685,16 @@ __device__ unsigned long long k4_item(const MatView M, uint32_t s, const Slot sl
     acc += x;
   }
   { const auto ret_ = (warp_sum64_ck(acc, ovf)); ovf_out |= ovf; return ret_; }
+}
+
+// Deadline check (batched and served passes): past the deadline, record
+// ST_TIMEOUT and stop taking roots and items.
+__device__ __forceinline__ bool past_deadline(const CountArgs &a) {
+  if (a.deadline_ns && globaltimer_ns() > a.deadline_ns) {
+    atomicOr(a.status, ST_TIMEOUT);
+    return true;
+  }
+  return false;
 }
 
 // graph of vertex u in a batch (last g with goff[g] <= u), and its k
@@ -839,7 +866,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
     __syncthreads();
     for (;;) {
       unsigned t = 0;
-      if (lane == 0) t = atomicAdd(&sh.next, 1u);
+      if (lane == 0) t = past_deadline(a) ? nitems : atomicAdd(&sh.next, 1u);
       t = __shfl_sync(0xffffffffu, t, 0);
       if (t >= nitems) break;
       unsigned long long item = 0;
@@ -859,9 +886,9 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
             if (k == 4) {
               item = k4_item<PV>(M, s, sl, ovf);
             } else if (k == 5 && (W <= 2 || s > cmax)) {
-              item = split_dispatch<PV>(M, s, 3, sl, ovf);  // one level below: compaction does not pay
+              item = split_dispatch<PV>(M, s, 3, sl, ovf, a.deadline_ns, a.status);  // compaction does not pay
             } else if (s <= cmax) {
-              item = compact_count<PV>(M, s, k - 2, sl, cnt, ovf);
+              item = compact_count<PV>(M, s, k - 2, sl, cnt, ovf, a.deadline_ns, a.status);
             }  // else (k >= 6): split into pair items
           }
         }
@@ -892,8 +919,8 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
           const uint64_t mw = lane < W ? (wv & rv[lane] & above_word(av, lane)) : 0ull;
           const uint32_t s0 = slot_set(sl, mw, W);
           if (s0 >= (uint32_t)(k - 3)) {
-            if (s0 <= cmax) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf);
-            else item = split_dispatch<PV>(M, s0, k - 3, sl, ovf);
+            if (s0 <= cmax) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf, a.deadline_ns, a.status);
+            else item = split_dispatch<PV>(M, s0, k - 3, sl, ovf, a.deadline_ns, a.status);
           }
         } else {
           if (lane == 0) atomicOr(a.status, ST_CAPACITY);
@@ -930,14 +957,6 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
   __syncthreads();
   ovf_out |= ovf;
   tsum_out = add_ck(tsum_out, tsum, ovf_out);
-}
-
-__device__ __forceinline__ bool past_deadline(const CountArgs &a) {
-  if (a.deadline_ns && globaltimer_ns() > a.deadline_ns) {
-    atomicOr(a.status, ST_TIMEOUT);
-    return true;
-  }
-  return false;
 }
 
 __device__ inline void finish_block(const CountArgs &a, unsigned long long tsum, unsigned ovf, unsigned long long *red,
@@ -1104,7 +1123,7 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_
     if (lane == 0) *w_next = 0;
     __syncwarp();
     for (;;) {
-      const unsigned t = atomicAdd(w_next, 1u);
+      const unsigned t = past_deadline(a) ? nitems : atomicAdd(w_next, 1u);
       if (t >= nitems) break;
       uint32_t i, jv = 0xffffffffu;
       uint64_t C[1];
@@ -1213,8 +1232,22 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
 
 template <bool PV, bool PA>
 cudaError_t occupancy_variant(size_t block_smem, int *block_per_sm, int *warp_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(count_block_kernel<PV, PA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)block_smem);
+  // The dynamic shared-memory limit of the block kernel is raised once to the
+  // device's opt-in maximum, not to this pass's size: plans made now may be
+  // launched later, after other plans (other sizes) were made.
+  static std::once_flag once;
+  static cudaError_t set_err = cudaSuccess;
+  std::call_once(once, [] {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    set_err = cudaGetDevice(&dev);
+    if (set_err == cudaSuccess) set_err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (set_err == cudaSuccess) set_err = cudaFuncGetAttributes(&fa, count_block_kernel<PV, PA>);
+    if (set_err == cudaSuccess)
+      set_err = cudaFuncSetAttribute(count_block_kernel<PV, PA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+  });
+  cudaError_t e = set_err;
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(block_per_sm, count_block_kernel<PV, PA>, kRootBlock,
                                                     block_smem);

@@ -347,6 +347,51 @@ def config_rmat20() -> Csr:
     return rmat(20, 16, 0.57, 0.19, 0.19, seed=2, permute=True)
 
 
+def chung_lu_planted_edges(n: int = 50_000_000, gamma: float = 2.1, mean_deg: float = 36.0, cliques: int = 1000,
+                           smin: int = 20, smax: int = 200, seed: int = 4, i0: float = 1.0):
+    """The endpoint pairs (before deduplication) of chung_lu_planted."""
+    eu, ev, _ = chung_lu_edges(n, gamma, mean_deg, seed, i0=i0)
+    sets = planted_sets(n, cliques, smin, smax, seed)
+    cu, cv = clique_pairs(sets)
+    return np.concatenate([eu, cu]), np.concatenate([ev, cv]), sets
+
+
+def csr_from_edges_on_device(n: int, eu, ev, device="cuda"):
+    """(row_ptr int64[n+1], col int32[nnz]) on `device` of the simple graph
+    spanned by the pairs: the same CSR as from_edges, built with torch sorts on
+    the device (for edge lists too large to sort quickly on the host). Input
+    preparation only: nothing of the counting method runs here."""
+    import torch
+    u = torch.from_numpy(np.ascontiguousarray(eu, dtype=np.uint32).view(np.int32)).to(device).to(torch.int64)
+    v = torch.from_numpy(np.ascontiguousarray(ev, dtype=np.uint32).view(np.int32)).to(device).to(torch.int64)
+    u &= 0xFFFFFFFF
+    v &= 0xFFFFFFFF
+    keep = u != v
+    u, v = u[keep], v[keep]
+    keys = torch.cat([(u << 32) | v, (v << 32) | u])
+    del u, v, keep
+    keys = torch.unique(keys, sorted=True)
+    rows = keys >> 32
+    col = (keys & 0xFFFFFFFF).to(torch.int32)
+    del keys
+    counts = torch.bincount(rows, minlength=n)
+    del rows
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(counts, 0, out=row_ptr[1:])
+    return row_ptr, col
+
+
+def chung_lu_planted(n: int = 50_000_000, gamma: float = 2.1, mean_deg: float = 36.0, cliques: int = 1000,
+                     smin: int = 20, smax: int = 200, seed: int = 4, i0: float = 1.0) -> Csr:
+    """Chung-Lu power-law graph (weights (i + i0)^(-1/(gamma-1)) scaled to the mean
+    degree and capped at sqrt(sum w); sum(w)/2 endpoint pairs drawn in proportion
+    to the weights, then deduplicated) plus `cliques` cliques of sizes uniform in
+    [smin, smax] planted on uniformly random vertex sets. The full-size default is
+    the 50M-vertex workload (about 0.9e9 edges)."""
+    eu, ev, _ = chung_lu_planted_edges(n, gamma, mean_deg, cliques, smin, smax, seed, i0)
+    return from_edges(n, eu, ev)
+
+
 @dataclass
 class BatchSpec:
     kind: str  # "er" or "ba"

@@ -59,6 +59,20 @@ class _Params(ctypes.Structure):
                 ("light_order", ctypes.c_uint32)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("grid_share_pct", ctypes.c_uint32), ("hbm_budget", ctypes.c_uint64)]
+
+
+class _RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("slot", ctypes.c_int), ("total", ctypes.c_uint64),
+                ("queue_ns", ctypes.c_uint64), ("run_ns", ctypes.c_uint64), ("latency_ns", ctypes.c_uint64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "admitted", "completed", "peak_in_flight",
+                                                "peak_bytes", "bytes_in_use", "queued")]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("sum_out_sq", ctypes.c_uint64), ("sum_arc_head", ctypes.c_uint64),
                 ("triangles", ctypes.c_uint64), ("max_out", ctypes.c_uint32)]
@@ -104,6 +118,17 @@ def _load():
         lib.kc_plan_free.argtypes = [P]
         lib.kc_plan_free.restype = None
         lib.kc_autotune_batched.argtypes = [P, BP, P, PP, ctypes.POINTER(ctypes.c_float), P]
+        lib.kc_server_create.argtypes = [ctypes.POINTER(_ServerConfig), ctypes.POINTER(P)]
+        lib.kc_server_submit.argtypes = [P, P, I, I, U64, ctypes.POINTER(U64)]
+        lib.kc_server_wait.argtypes = [P, U64, I, ctypes.POINTER(_RequestResult)]
+        lib.kc_server_fetch_per_vertex.argtypes = [P, U64, P, P]
+        lib.kc_server_release.argtypes = [P, U64]
+        lib.kc_server_get_stats.argtypes = [P, ctypes.POINTER(_ServerStats)]
+        lib.kc_server_destroy.argtypes = [P]
+        lib.kc_server_destroy.restype = None
+        for f in (lib.kc_server_create, lib.kc_server_submit, lib.kc_server_wait, lib.kc_server_fetch_per_vertex,
+                  lib.kc_server_release, lib.kc_server_get_stats):
+            f.restype = I
         lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         lib.kc_measure_word_op_rate.restype = I
         lib.kc_kernel_launches.argtypes = []
@@ -319,6 +344,65 @@ def kc_autotune_batched(dag: Dag, batch: Batch, out: torch.Tensor | None = None,
                                        _stream(stream)))
     return ({"light_max": int(p.light_max), "compact_max": int(p.compact_max), "chunk": int(p.chunk),
              "light_order": int(p.light_order)}, float(ms.value))
+
+
+class Server:
+    """kc_server: continuous-batching request loop on device-resident DAGs.
+
+    submit() queues a request and returns its id; wait() returns a dict with the
+    request's status, total and host-clock times (seconds); per-vertex results
+    are fetched with fetch_per_vertex() and then release()d."""
+
+    def __init__(self, slots: int = 8, hbm_budget: int = 8 << 30, grid_share_pct: int = 0):
+        cfg = _ServerConfig(int(slots), int(grid_share_pct), int(hbm_budget))
+        h = ctypes.c_void_p()
+        _check(_load().kc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._dags = {}
+
+    def submit(self, dag: Dag, k: int, per_vertex: bool = False, timeout_us: int = 0) -> int:
+        rid = ctypes.c_uint64()
+        _check(_load().kc_server_submit(self._h, dag.handle, int(k), 1 if per_vertex else 0, int(timeout_us),
+                                        ctypes.byref(rid)))
+        self._dags[int(rid.value)] = dag  # keep the DAG alive while the request lives
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> dict:
+        r = _RequestResult()
+        _check(_load().kc_server_wait(self._h, int(rid), int(timeout_ms), ctypes.byref(r)))
+        return {"status": int(r.status), "slot": int(r.slot), "total": int(r.total), "queue_s": r.queue_ns * 1e-9,
+                "run_s": r.run_ns * 1e-9, "latency_s": r.latency_ns * 1e-9}
+
+    def fetch_per_vertex(self, rid: int, out: torch.Tensor, stream=None) -> torch.Tensor:
+        if not out.is_contiguous() or out.dtype != torch.int64:
+            raise ValueError("out must be a contiguous int64 tensor")
+        _check(_load().kc_server_fetch_per_vertex(self._h, int(rid), out.data_ptr(), _stream(stream)))
+        return out
+
+    def release(self, rid: int):
+        _check(_load().kc_server_release(self._h, int(rid)))
+        self._dags.pop(int(rid), None)
+
+    def forget(self, rid: int):
+        """Drop the DAG reference of a count request after its wait()."""
+        self._dags.pop(int(rid), None)
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(_load().kc_server_get_stats(self._h, ctypes.byref(st)))
+        return {f: int(getattr(st, f)) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._h and self._h.value:
+            _load().kc_server_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+            self._dags.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kc_dag_get_stats(dag: Dag, stream=None) -> dict:
