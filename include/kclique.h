@@ -213,7 +213,8 @@ typedef struct {
  *                KC_LIGHT_BY_DEGREE = decreasing out-degree (load balance),
  *                KC_LIGHT_BY_ID = increasing vertex id (locality: a batch's
  *                graphs are counted one id range at a time, so their
- *                out-lists stay in L2); 0 = id order for batches
+ *                out-lists stay in L2, but 32 consecutive ids go to one
+ *                warp); 0 = by out-degree
  * Every setting gives the same counts; only the speed differs.
  */
 #define KC_LIGHT_BY_DEGREE 1

@@ -224,8 +224,7 @@ void set_work(CountArgs *a, uint8_t *w) {
 // Kernel configuration for a counting pass over d with smallest k = k_min:
 // shared-memory capacity of a block root, grids from the occupancy, the root
 // ranges of the order array, and the global scratch the largest roots need.
-cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_params *prm, bool batched,
-                       LaunchPlan *out) {
+cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_params *prm, LaunchPlan *out) {
   LaunchPlan &P = *out;
   memset(&P, 0, sizeof P);
   int dev = 0, optin = 0;
@@ -256,7 +255,7 @@ cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_pa
   a.compact_max = prm ? prm->compact_max : 0;
   a.chunk = prm ? prm->chunk : 0;
   const uint32_t lo = prm ? prm->light_order : 0u;
-  a.light_by_id = (lo == KC_LIGHT_BY_ID || (lo == 0 && batched)) ? 1u : 0u;
+  a.light_by_id = lo == KC_LIGHT_BY_ID ? 1u : 0u;
   a.n = d->n;
   a.light_min = (uint32_t)(k_min - 1);
   a.light_max = light;
@@ -302,7 +301,7 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
   }
   if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
   LaunchPlan P;
-  KC_CK(plan_count(d, k, pv != nullptr, pa != nullptr, nullptr, false, &P));
+  KC_CK(plan_count(d, k, pv != nullptr, pa != nullptr, nullptr, &P));
   CountArgs &a = P.a;
   a.pv = pv;
   a.pa = pa;

@@ -45,12 +45,10 @@ struct DevBuf {
 };
 
 // Kernel configuration for a counting pass over d whose smallest clique size
-// is k_min; prm may be null (defaults; warp roots in vertex-id order for a
-// batch, by out-degree otherwise). Fills everything in P.a except the
+// is k_min; prm may be null (defaults: warp roots by out-degree). Fills everything in P.a except the
 // outputs, the work block and the scratch pointer; P.scratch_bytes is the
 // global scratch the largest roots need (0 if none).
-cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_params *prm, bool batched,
-                       LaunchPlan *P);
+cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_params *prm, LaunchPlan *P);
 
 kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned long long *pa, uint64_t *h_total,
                     uint64_t deadline_ns, cudaStream_t s);

@@ -280,7 +280,7 @@ kc_status kc_server_submit(kc_server *s, const kc_dag *d, int k, int per_vertex,
   r.t_submit = now_ns();
   r.timeout_us = timeout_us;
   if ((uint32_t)(k - 1) <= d->max_out) {
-    cudaError_t e = kc::plan_count(d, k, r.pv, false, nullptr, false, &r.plan);
+    cudaError_t e = kc::plan_count(d, k, r.pv, false, nullptr, &r.plan);
     if (e != cudaSuccess) return kc::cuda_fail(e);
   } else {
     memset(&r.plan, 0, sizeof r.plan);  // no root can hold a k-clique: nothing to launch
