@@ -1189,43 +1189,58 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
   unsigned long long tsum = 0;
   uint8_t *slot = smem + (size_t)warp * light_layout(PV, PA).bytes;
   const uint32_t chunk = a.chunk ? a.chunk : 1u;
-  if (a.light_by_id) {
-    // Roots in vertex-id order, so that a batch's graphs are counted one
-    // region at a time and their out-lists stay in L2: each pull takes
-    // 32*chunk ids, lanes test 32 of them at once, the warp counts the
-    // qualifying ones (light_min <= d+ <= light_max) in id order.
-    for (;;) {
-      unsigned idx = 0;
-      if (lane == 0) idx = past_deadline(a) ? 0xffffffffu : atomicAdd(&a.queue[2], chunk);
-      idx = __shfl_sync(0xffffffffu, idx, 0);
-      if (idx == 0xffffffffu || (unsigned long long)idx * 32ull >= a.n) break;
-      const uint32_t lo = idx * 32u, hi = (uint32_t)min((unsigned long long)a.n, (unsigned long long)(idx + chunk) * 32ull);
-      for (uint32_t base = lo; base < hi; base += 32) {
-        const uint32_t u = base + lane;
+  const uint32_t nlight = a.n_light_end - a.n_big;
+  const unsigned long long ngroups = ((unsigned long long)a.n + 31ull) / 32ull;
+  // One call site of warp_root (its body is large). The warp-uniform cursor walks the work
+  // this warp pulled: positions of the order array (out-degree order) or
+  // groups of 32 vertex ids whose qualifying members (light_min <= d+ <=
+  // light_max) are taken in id order (id order: a batch's graphs are counted
+  // one id range at a time, so their out-lists stay in L2).
+  uint32_t q = 0, qend = 0, base = 0;
+  unsigned mask = 0;
+  for (;;) {
+    uint32_t u;
+    if (a.light_by_id) {
+      bool done = false;
+      while (mask == 0) {
+        if (q >= qend) {
+          unsigned idx = 0;
+          if (lane == 0) idx = past_deadline(a) ? 0xffffffffu : atomicAdd(&a.queue[2], chunk);
+          idx = __shfl_sync(0xffffffffu, idx, 0);
+          if ((unsigned long long)idx >= ngroups) {
+            done = true;
+            break;
+          }
+          q = idx;
+          qend = (uint32_t)min(ngroups, (unsigned long long)idx + chunk);
+        }
+        base = q * 32u;
+        ++q;
+        const uint32_t v = base + lane;
         bool ok = false;
-        if (u < hi) {
-          const uint32_t d = (uint32_t)(a.ptr[u + 1] - a.ptr[u]);
+        if (v < a.n) {
+          const uint32_t d = (uint32_t)(a.ptr[v + 1] - a.ptr[v]);
           ok = d >= a.light_min && d <= a.light_max;
         }
-        unsigned mask = __ballot_sync(0xffffffffu, ok);
-        while (mask) {
-          const int l = __ffs(mask) - 1;
-          mask &= mask - 1;
-          warp_root<PV, PA>(a, base + (uint32_t)l, slot, tsum, ovf, &w_next[warp]);
-        }
+        mask = __ballot_sync(0xffffffffu, ok);
       }
+      if (done) break;
+      const int l = __ffs(mask) - 1;
+      mask &= mask - 1;
+      u = base + (uint32_t)l;
+    } else {
+      if (q >= qend) {
+        unsigned idx = 0;
+        if (lane == 0) idx = past_deadline(a) ? 0xffffffffu : atomicAdd(&a.queue[2], chunk);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= nlight) break;
+        q = idx;
+        qend = min(nlight, idx + chunk);
+      }
+      u = a.order[a.n_big + q];
+      ++q;
     }
-    finish_block(a, tsum, ovf, red, kWarps);
-    return;
-  }
-  const uint32_t nlight = a.n_light_end - a.n_big;
-  for (;;) {
-    unsigned idx = 0;
-    if (lane == 0) idx = past_deadline(a) ? 0xffffffffu : atomicAdd(&a.queue[2], chunk);
-    idx = __shfl_sync(0xffffffffu, idx, 0);
-    if (idx >= nlight) break;
-    const uint32_t end = min(nlight, idx + chunk);
-    for (uint32_t q = idx; q < end; ++q) warp_root<PV, PA>(a, a.order[a.n_big + q], slot, tsum, ovf, &w_next[warp]);
+    warp_root<PV, PA>(a, u, slot, tsum, ovf, &w_next[warp]);
   }
   finish_block(a, tsum, ovf, red, kWarps);
 }
