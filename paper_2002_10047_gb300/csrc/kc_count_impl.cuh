@@ -1190,12 +1190,18 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
   uint8_t *slot = smem + (size_t)warp * light_layout(PV, PA).bytes;
   const uint32_t chunk = a.chunk ? a.chunk : 1u;
   const uint32_t nlight = a.n_light_end - a.n_big;
-  const unsigned long long ngroups = ((unsigned long long)a.n + 31ull) / 32ull;
-  // One call site of warp_root (its body is large). The warp-uniform cursor walks the work
-  // this warp pulled: positions of the order array (out-degree order) or
-  // groups of 32 vertex ids whose qualifying members (light_min <= d+ <=
-  // light_max) are taken in id order (id order: a batch's graphs are counted
-  // one id range at a time, so their out-lists stay in L2).
+  // id order walks windows of 2^16 ids; inside a window, slot s holds the id
+  // with the bit-reversed offset, so the ids one warp takes are spread over
+  // the window (a graph's consecutive densest roots land in different warps)
+  // while all warps stay in one L2-resident window of the batch
+  constexpr uint32_t kWinBits = 16;
+  const unsigned long long ngroups =
+      (((unsigned long long)a.n + (1ull << kWinBits) - 1) >> kWinBits) << (kWinBits - 5);
+  // One call site of warp_root (its body is large). The warp-uniform cursor
+  // walks the work this warp pulled: positions of the order array (out-degree
+  // order) or groups of 32 id slots whose qualifying members (light_min <= d+
+  // <= light_max) are taken in slot order (id order: a batch's graphs are
+  // counted one id window at a time, so their out-lists stay in L2).
   uint32_t q = 0, qend = 0, base = 0;
   unsigned mask = 0;
   for (;;) {
@@ -1216,7 +1222,8 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
         }
         base = q * 32u;
         ++q;
-        const uint32_t v = base + lane;
+        const uint32_t slot_i = base + lane;
+        const uint32_t v = (slot_i & ~((1u << kWinBits) - 1u)) | (__brev(slot_i) >> (32 - kWinBits));
         bool ok = false;
         if (v < a.n) {
           const uint32_t d = (uint32_t)(a.ptr[v + 1] - a.ptr[v]);
@@ -1227,7 +1234,8 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
       if (done) break;
       const int l = __ffs(mask) - 1;
       mask &= mask - 1;
-      u = base + (uint32_t)l;
+      const uint32_t slot_l = base + (uint32_t)l;
+      u = (slot_l & ~((1u << kWinBits) - 1u)) | (__brev(slot_l) >> (32 - kWinBits));
     } else {
       if (q >= qend) {
         unsigned idx = 0;

@@ -175,7 +175,7 @@ def test_batch_full_4096_bit_exact(kc):
     want = oracle_totals(graphs, ks)
     dag, b = device_batch(kc, graphs, ks)
     del graphs
-    for params in (None, (0, 0, 0, kc.KC_LIGHT_BY_DEGREE)):
+    for params in (None, (0, 0, 16, kc.KC_LIGHT_BY_ID)):
         tot, out = kc.count_batched(dag, b, params=params)
         got = kc.as_uint64(out)
         assert np.array_equal(got, want), (params, np.nonzero(got != want)[0][:10])
