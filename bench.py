@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--grid-share", type=int, default=50, help="serve: percent of the full grid per request")
     ap.add_argument("--request-timeout-ms", type=int, default=1000)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the compact batch and serving measurements")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     return ap.parse_args()
 
@@ -225,6 +227,95 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------- ours
+def batch_and_serving_summary(args, kc, dev):
+    """Compact forms of the batch and serving workloads for the default line:
+    one tuned batched pass (CUDA-graph replay, timed over the steps) against one
+    library call per graph, and the request stream at one rate for continuous
+    batching and for one request at a time."""
+    import torch
+
+    from paper_2002_10047_gb300 import graphgen as gg
+    out = {}
+    specs, graphs = make_batch(4096)
+    u, off = gg.concat_csr(graphs)
+    ks_np = np.array([sp.k for sp in specs], dtype=np.uint8)
+    rp, col = kc.csr_to_device(u, dev)
+    dag = kc.orient(rp, col, u.n, method="degree")
+    batch = kc.Batch(torch.from_numpy(off.view(np.int64)).to(dev), torch.from_numpy(ks_np).to(dev))
+    params = {"light_max": 64, "compact_max": 64, "chunk": 16, "light_order": 1}  # the autotuner's choice
+    plan = kc.Plan(dag, batch, params=params)
+    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        plan.launch()
+    stream.wait_stream(side)
+    total = plan.result()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg):
+        plan.launch()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        cg.replay()
+    ms = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        cg.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    assert plan.result() == total
+    plan.free()
+    t_batch = sum(ms) / len(ms)
+    rp_h = u.row_ptr.view(np.int64)
+    per = []
+    for i in range(len(graphs)):
+        v0, v1 = int(off[i]), int(off[i + 1])
+        e0, e1 = int(rp_h[v0]), int(rp_h[v1])
+        per.append(kc.orient(rp[v0:v1 + 1] - e0, col[e0:e1] - v0, v1 - v0) if v1 > v0 else None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tot_pg = sum(kc.count(d, int(ks_np[i])) for i, d in enumerate(per) if d is not None)
+    t_pg = (time.perf_counter() - t0) * 1e3
+    assert tot_pg == total
+    for d in per:
+        if d is not None:
+            d.free()
+    dag.free()
+    del rp, col, flush
+    out["batch"] = {"workload": batch_workload(len(graphs)), "graphs_per_s": len(graphs) / (t_batch / 1e3),
+                    "ms_per_pass": t_batch, "cliques_per_pass": total, "params": params,
+                    "one_call_per_graph": {"graphs_per_s": len(graphs) / (t_pg / 1e3), "ms_per_pass": t_pg},
+                    "speedup_vs_one_call_per_graph": t_pg / t_batch}
+    pool = make_pool(args)
+    dags, ns = [], []
+    for g in pool:
+        grp, gcol = kc.csr_to_device(g, dev)
+        dags.append(kc.orient(grp, gcol, g.n, method="degree"))
+        ns.append(g.n)
+    rate = 100.0
+    serving = {"workload": serve_workload(args, rates="100", requests=300), "rate": rate, "requests": 300}
+    for mode, slots, share in (("continuous", args.slots, args.grid_share), ("one_at_a_time", 1, 100)):
+        srv = kc.Server(slots=slots, hbm_budget=8 << 30, grid_share_pct=share)
+        try:
+            _drive(kc, srv, dags, ns, serve_requests(64, 1e5, 99), args.request_timeout_ms * 1000)
+            res, span = _drive(kc, srv, dags, ns, serve_requests(300, rate, 5), args.request_timeout_ms * 1000)
+        finally:
+            srv.close()
+        lat = np.array([r["latency_s"] for r in res]) * 1e3
+        serving[mode] = {"slots": slots, "grid_share_pct": share, "throughput": len(res) / span,
+                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "ok": int(sum(r["status"] == kc.KC_OK for r in res)),
+                         "timed_out": int(sum(r["status"] == kc.KC_ETIMEDOUT for r in res))}
+    for d in dags:
+        d.free()
+    out["serving"] = serving
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -405,6 +496,8 @@ def run_ours(args, rank, world):
     }
     if e2e:
         line["e2e"] = e2e
+    if not args.no_extras:
+        line.update(batch_and_serving_summary(args, kc, dev))
     if not args.no_cpu_baseline:
         cores = host_cores()
         rate, cl, secs, desc = oracle_rate(g, ks, args.cpu_seconds, cores)
@@ -696,10 +789,12 @@ SERVE_METRIC = "served requests/s at p99 latency"
 SERVE_UNIT = "req/s"
 
 
-def serve_workload(args) -> str:
+def serve_workload(args, rates=None, requests=None) -> str:
+    rates = args.rates if rates is None else rates
+    requests = args.requests if requests is None else requests
     return (f"pool of 200 resident graphs, seed 5: 100 R-MAT (scale U{{10..{args.pool_max_scale}}}, edge factor "
             f"U{{8..{args.pool_max_ef}}}) and 100 Erdos-Renyi (n U[1000,{args.pool_max_er}], average degree U[4,64]); Poisson "
-            f"arrivals at {args.rates} req/s, {args.requests} requests per rate; k U{{3..9}}, count or "
+            f"arrivals at {rates} req/s, {requests} requests per rate; k U{{3..9}}, count or "
             "per-vertex count 50/50; admission by device-memory footprint")
 
 
