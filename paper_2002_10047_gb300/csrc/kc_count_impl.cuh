@@ -63,6 +63,14 @@ __device__ __forceinline__ void atomic_add_ck(unsigned long long *p, unsigned lo
   ovf |= (old + v < old) ? ST_OVERFLOW : 0u;
 }
 
+// Adds into a root's (or an item's) local per-vertex counters. No wrap check
+// is needed: an entry counts cliques of that root containing the vertex, so
+// it never exceeds the root's total, whose additions are checked; the flush
+// into the global per-vertex array is checked again.
+__device__ __forceinline__ void cnt_add(unsigned long long *p, unsigned long long v) {
+  if (v) atomicAdd(p, v);
+}
+
 __device__ __forceinline__ unsigned long long warp_sum64_ck(unsigned long long v, unsigned &ovf) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -258,7 +266,7 @@ __device__ __forceinline__ unsigned long long leaf2(const uint64_t (&C)[NW], con
 #pragma unroll
         for (int r = 0; r < NW; ++r) a += __popcll(C[r] & R[r]);
         a = gsum32<G>(a);
-        if (j == 0 && a) atomic_add_ck(&V.cnt[x], a, ovf);
+        if (j == 0 && a) cnt_add(&V.cnt[x], a);
       } else {
 #pragma unroll
         for (int r = 0; r < NW; ++r) a += __popcll(T[r] & R[r]);
@@ -307,7 +315,7 @@ __device__ __forceinline__ unsigned long long dfs_fixed(const uint64_t (&C)[NW],
         if ((int)c < L - 1) continue;
         const unsigned long long sub = dfs_fixed<G, NW, PV, L - 1>(Cn, V, j, ovf);
         sum = add_ck(sum, sub, ovf);
-        if (PV) atomic_add_ck(&V.cnt[x], sub, ovf);
+        if (PV) cnt_add(&V.cnt[x], sub);
       }
     } else {
       uint64_t T[NW];
@@ -327,7 +335,7 @@ __device__ __forceinline__ unsigned long long dfs_fixed(const uint64_t (&C)[NW],
         if ((int)c < L - 1) continue;
         const unsigned long long sub = dfs_fixed<G, NW, PV, L - 1>(Cn, V, j, ovf);
         sum = add_ck(sum, sub, ovf);
-        if (PV && j == 0) atomic_add_ck(&V.cnt[x], sub, ovf);
+        if (PV && j == 0) cnt_add(&V.cnt[x], sub);
       }
     }
     ovf_out |= ovf;
@@ -397,7 +405,7 @@ __device__ unsigned long long dfs_stack(const uint64_t (&C0)[NW], int ell, const
       }
       --top;
       subs[top] = add_ck(subs[top], a, ovf);
-      if (PV && j == 0) atomic_add_ck(&V.cnt[xs[top]], a, ovf);
+      if (PV && j == 0) cnt_add(&V.cnt[xs[top]], a);
     }
   }
   { const auto ret_ = (ret); ovf_out |= ovf; return ret_; }
@@ -549,7 +557,7 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
       if (picks == 2) sub = (unsigned long long)pc;
       else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, 2, PV>(C, picks - 1, V, 0, ovf);
     }
-    if (PV && picks > 2 && sub) atomic_add_ck(&sl.cs[q], sub, ovf);
+    if (PV && picks > 2 && sub) cnt_add(&sl.cs[q], sub);
     acc = add_ck(acc, sub, ovf);
   }
   if (PV && picks == 2) {
@@ -557,7 +565,7 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
     for (uint32_t q = lane; q < s; q += 32) {
       unsigned b = (unsigned)__popcll(sl.S[q * NWc]);
       if (NWc == 2) b += (unsigned)__popcll(sl.S[q * NWc + 1]);
-      if (b) atomic_add_ck(&sl.cs[q], b, ovf);
+      if (b) cnt_add(&sl.cs[q], b);
     }
   }
   __syncwarp();
@@ -591,7 +599,7 @@ __device__ unsigned long long split_count(const MatView M, uint32_t s, int picks
     unsigned long long sub = 0;
     if (picks == 2) sub = (unsigned long long)pc;
     else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, NW, PV>(C, picks - 1, M, 0, ovf);
-    if (PV && picks > 2 && sub) atomic_add_ck(&M.cnt[x], sub, ovf);
+    if (PV && picks > 2 && sub) cnt_add(&M.cnt[x], sub);
     acc = add_ck(acc, sub, ovf);
   }
   if (PV && picks == 2) {
@@ -601,7 +609,7 @@ __device__ unsigned long long split_count(const MatView M, uint32_t s, int picks
       const uint64_t *cy = M.adj + (size_t)y * M.RS;
       unsigned b = 0;
       for (uint32_t w = 0; w < W; ++w) b += (unsigned)__popcll(sl.mask[w] & cy[w]);
-      if (b) atomic_add_ck(&M.cnt[y], b, ovf);
+      if (b) cnt_add(&M.cnt[y], b);
     }
   }
   __syncwarp();
@@ -681,7 +689,7 @@ __device__ unsigned long long k4_item(const MatView M, uint32_t s, const Slot sl
       x += (unsigned)__popcll(m & above_word(q, z));
       if (PV) yv += (unsigned)__popcll(m);
     }
-    if (PV && yv) atomic_add_ck(&M.cnt[q], yv, ovf);
+    if (PV && yv) cnt_add(&M.cnt[q], yv);
     acc += x;
   }
   { const auto ret_ = (warp_sum64_ck(acc, ovf)); ovf_out |= ovf; return ret_; }
@@ -930,8 +938,8 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
       if (lane == 0 && item) {
         rsum = add_ck(rsum, item, ovf);
         if (PV) {
-          atomic_add_ck(&cnt[i], item, ovf);
-          if (av != 0xffffffffu) atomic_add_ck(&cnt[av], item, ovf);
+          cnt_add(&cnt[i], item);
+          if (av != 0xffffffffu) cnt_add(&cnt[av], item);
         }
         if (PA) atomic_add_ck(&asub[i], item, ovf);
       }
@@ -1157,8 +1165,8 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_
       const unsigned long long s = dfs<1, 1, PV>(C, ell, V, 0, ovf);
       rsum = add_ck(rsum, s, ovf);
       if (PV) {
-        atomic_add_ck(&cnt[i], s, ovf);
-        if (jv != 0xffffffffu) atomic_add_ck(&cnt[jv], s, ovf);
+        cnt_add(&cnt[i], s);
+        if (jv != 0xffffffffu) cnt_add(&cnt[jv], s);
       }
       if (PA) atomic_add_ck(&asub[i], s, ovf);
     }
