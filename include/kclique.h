@@ -331,6 +331,39 @@ kc_status kc_server_get_stats(kc_server *s, kc_server_stats *out);
 void kc_server_destroy(kc_server *s);
 
 /*
+ * kc_peel -- arb-peel (Algorithm 2, Section 4.1): exact k-clique peeling for
+ * the k-clique densest subgraph, seeded by arb-count-v. Each round removes
+ * every remaining vertex whose current k-clique count (in the graph induced
+ * by the remaining vertices) is the minimum; Update counts the k-cliques
+ * that the round removes (a clique with several vertices of the round is
+ * counted at the lowest-ranked of them) and lowers the counts of the
+ * remaining vertices. The result is the largest density (k-cliques per
+ * vertex) among the graph itself and what remains after each round; the
+ * paper proves it is at least 1/k of the k-clique densest subgraph's.
+ *   g        the CSR d was oriented from (the undirected neighbour lists are
+ *            read during the call)
+ *   d        kc_orient(g, ...) (either method; the result does not depend
+ *            on it)
+ *   k        3 .. KC_KMAX
+ *   d_round  device uint32[n], caller-owned: the round in which each vertex
+ *            is removed (0-based)
+ *   out      rounds: number of rounds; best_cliques / best_vertices: the best
+ *            density as an exact fraction, reached by the vertices removed
+ *            in rounds >= best_rounds (best_rounds = 0: the whole graph);
+ *            total: k-cliques of the whole graph
+ * Synchronises `stream` every round. KC_EINVAL if g and d differ in size.
+ */
+typedef struct {
+  uint32_t rounds;
+  uint32_t best_rounds;
+  uint64_t best_cliques;
+  uint64_t best_vertices;
+  uint64_t total;
+} kc_peel_result;
+kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *d_round, kc_peel_result *out,
+                  kc_stream_t stream);
+
+/*
  * Work statistics of an oriented graph, used for the bytes a counting pass
  * must move (computed exactly on the device):
  *   sum_out_sq     sum over roots u of d+(u)^2

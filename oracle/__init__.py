@@ -14,6 +14,10 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   cliques, and the 4-clique fragment of the paper's worked example
   (Appendix A, Figure 7; the figure itself is missing, so that pin is partial).
 * ``count_arc``: sums over all arcs equal ``count`` (k >= 2).
+* ``peel`` (arb-peel, Algorithm 2): K_n in one round at C(n,k)/n; a disjoint
+  K_a + K_b in two rounds at C(b,k)/b; no k-clique -> one round at 0; the
+  1/k guarantee against a brute-force densest subset (n <= 12); peeling
+  rounds follow a relabelling of the vertices.
 * ``orient`` (degree / degeneracy / original / gp): every ordering yields an
   acyclic orientation that keeps each edge once; the degree and GP orders
   are checked against their defining properties on hand-made graphs.
@@ -264,3 +268,77 @@ def timed_count(g, k: int, threads: int, method: str = "degree", max_seconds: fl
         tot += count(dag, k, threads=threads, lo=done, hi=hi)
         done = hi
     return tot, time.perf_counter() - t0, done
+
+
+@dataclass
+class PeelResult:
+    rounds: int
+    best_rounds: int
+    best_cliques: int
+    best_vertices: int
+    total: int
+
+
+def _induced(g, keep: np.ndarray):
+    """The subgraph induced by the vertices with keep[v], relabelled 0..n'-1
+    in id order (so that its vertex i is the i-th kept id)."""
+    ids = np.nonzero(keep)[0]
+    new = np.full(g.n, -1, dtype=np.int64)
+    new[ids] = np.arange(ids.size)
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr.astype(np.int64)))
+    dst = g.col.astype(np.int64)
+    sel = keep[src] & keep[dst]
+    s2, d2 = new[src[sel]], new[dst[sel]]
+    n2 = ids.size
+    order = np.lexsort((d2, s2))
+    s2, d2 = s2[order], d2[order]
+    row_ptr = np.zeros(n2 + 1, dtype=np.uint64)
+    np.cumsum(np.bincount(s2, minlength=n2), out=row_ptr[1:])
+    return _G(n2, row_ptr, d2.astype(np.uint32)), ids
+
+
+@dataclass
+class _G:
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+
+def peel(g, k: int):
+    """arb-peel (Algorithm 2) by its definition: every round removes all
+    remaining vertices whose k-clique count in the graph induced by the
+    remaining vertices is the minimum; the counts are recomputed from scratch
+    on the remaining graph each round (the paper's Update keeps the same
+    counts incrementally). The best density (k-cliques per vertex) over the
+    graph itself and every remainder is kept as an exact fraction.
+    Returns (PeelResult, rounds int64[n])."""
+    n = g.n
+    rounds = np.full(n, -1, dtype=np.int64)
+    keep = np.ones(n, dtype=bool)
+    total = None
+    best = None
+    r = 0
+    while keep.any():
+        sub, ids = _induced(g, keep)
+        t, pv = count_per_vertex(orient(sub, "degree"), k)
+        if total is None:
+            total = t
+            best = (t, n, 0)
+        mn = pv.min()
+        peel_now = ids[pv == mn]
+        rounds[peel_now] = r
+        keep[peel_now] = False
+        remaining = int(keep.sum())
+        if remaining:
+            sub2, _ = _induced(g, keep)
+            t2 = count(orient(sub2, "degree"), k)
+            if t2 * best[1] > best[0] * remaining:
+                best = (t2, remaining, r + 1)
+        r += 1
+    if total is None:
+        total, best = 0, (0, 0, 0)
+    return PeelResult(r, best[2], best[0], best[1], total), rounds

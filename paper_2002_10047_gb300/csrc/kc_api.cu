@@ -80,6 +80,7 @@ void kc_dag_free(kc_dag *d) {
   if (d->ptr) cudaFreeAsync(d->ptr, d->stream);
   if (d->col) cudaFreeAsync(d->col, d->stream);
   if (d->order) cudaFreeAsync(d->order, d->stream);
+  if (d->key) cudaFreeAsync(d->key, d->stream);
   delete d;
 }
 
@@ -174,6 +175,7 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   auto ge = [&](uint64_t t) -> uint32_t { return t < D->ge.size() ? (uint32_t)D->ge[t] : 0u; };
   KC_CK(kc::launch_sort_rows(D->ptr, D->col, key.as<uint64_t>(), D->order, ge(1025), ge(33), ge(2), maxd, s));
   KC_CK(cudaStreamSynchronize(s));  // `start` is a pageable host buffer read by the copy above
+  D->key = (uint64_t *)key.release();  // kept: peeling compares ranks
   *out = D;
   guard.d = nullptr;
   return KC_OK;

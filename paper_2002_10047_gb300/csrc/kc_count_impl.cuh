@@ -743,10 +743,15 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
   unsigned ovf = 0;
   unsigned long long tsum = 0;
   const unsigned tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-  const uint64_t b = a.ptr[u];
-  const uint32_t d = (uint32_t)(a.ptr[u + 1] - b);
+  // root rows: the DAG's out-lists, or (peeling) separate candidate rows
+  // indexed like `order`, with the root's vertex id in rvert
+  const uint64_t *rp_ = a.rptr ? a.rptr : a.ptr;
+  const uint32_t *rc_ = a.rptr ? a.rcol : a.col;
+  const uint64_t b = rp_[u];
+  const uint32_t d = (uint32_t)(rp_[u + 1] - b);
+  const uint32_t uv = a.rptr ? a.rvert[u] : u;
   const uint32_t W = words_of(d), T = hash_slots(d);
-  const uint32_t g = a.goff ? graph_of(a, u) : 0u;
+  const uint32_t g = a.goff ? graph_of(a, uv) : 0u;
   const int k = a.goff ? (int)a.gk[g] : a.k;
   if (k < 3 || k > KC_KMAX) {  // batches only: k = 1, 2 have closed forms, larger k is rejected
     if ((threadIdx.x & 31) == 0) atomicOr(a.status, ST_BAD_ARG);
@@ -769,7 +774,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
   const uint32_t per = (d + kRootBlock - 1) / kRootBlock;
   const uint32_t c0 = min(d, tid * per), c1 = min(d, c0 + per);
   for (uint32_t i = tid; i < d; i += kRootBlock) {
-    const uint32_t x = a.col[b + i];
+    const uint32_t x = rc_[b + i];
     const uint64_t xb = a.ptr[x];
     L[i] = x;
     rb[i] = xb;
@@ -953,7 +958,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
     if (tid == 0) {
       unsigned long long t = 0;
       for (int w = 0; w < kRootWarps; ++w) t = add_ck(t, sh.red[w], ovf);
-      if (PV) atomic_add_ck(&a.pv[u], t, ovf);
+      if (PV) atomic_add_ck(&a.pv[uv], t, ovf);
       if (a.gtotal) atomic_add_ck(&a.gtotal[g], t, ovf);
     }
     if (PV)
@@ -1036,9 +1041,14 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_
   unsigned long long *asub = PA ? (unsigned long long *)(slot + o.asub) : nullptr;
   uint32_t *pre = (uint32_t *)(slot + o.pre);
   uint32_t *epre = (uint32_t *)(slot + o.epre);
-  const uint64_t b = a.ptr[u];
-  const uint32_t d = (uint32_t)(a.ptr[u + 1] - b);
-  const uint32_t g = a.goff ? graph_of(a, u) : 0u;
+  // root rows: the DAG's out-lists, or (peeling) separate candidate rows
+  // indexed like `order`, with the root's vertex id in rvert
+  const uint64_t *rp_ = a.rptr ? a.rptr : a.ptr;
+  const uint32_t *rc_ = a.rptr ? a.rcol : a.col;
+  const uint64_t b = rp_[u];
+  const uint32_t d = (uint32_t)(rp_[u + 1] - b);
+  const uint32_t uv = a.rptr ? a.rvert[u] : u;
+  const uint32_t g = a.goff ? graph_of(a, uv) : 0u;
   const int k = a.goff ? (int)a.gk[g] : a.k;
   if (k < 3 || k > KC_KMAX) {  // batches only: k = 1, 2 have closed forms, larger k is rejected
     if ((threadIdx.x & 31) == 0) atomicOr(a.status, ST_BAD_ARG);
@@ -1053,14 +1063,14 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_
   for (uint32_t s = lane; s < 128; s += 32) hkey[s] = kEmpty;
   uint32_t e0 = 0, e1 = 0;
   if (lane < d) {
-    const uint32_t x = a.col[b + lane];
+    const uint32_t x = rc_[b + lane];
     const uint64_t xb = a.ptr[x];
     L[lane] = x;
     rbeg[lane] = xb;
     e0 = (uint32_t)(a.ptr[x + 1] - xb);
   }
   if (lane + 32 < d) {
-    const uint32_t x = a.col[b + lane + 32];
+    const uint32_t x = rc_[b + lane + 32];
     const uint64_t xb = a.ptr[x];
     L[lane + 32] = x;
     rbeg[lane + 32] = xb;
@@ -1174,7 +1184,7 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_
   __syncwarp();
   if (PV || a.gtotal) {
     const unsigned long long t = warp_sum64_ck(rsum, ovf);
-    if (lane == 0 && PV) atomic_add_ck(&a.pv[u], t, ovf);
+    if (lane == 0 && PV) atomic_add_ck(&a.pv[uv], t, ovf);
     if (lane == 0 && a.gtotal) atomic_add_ck(&a.gtotal[g], t, ovf);
     if (PV)
       for (uint32_t i = lane; i < d; i += 32) atomic_add_ck(&a.pv[L[i]], cnt[i], ovf);

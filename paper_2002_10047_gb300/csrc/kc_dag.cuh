@@ -12,6 +12,7 @@ struct kc_dag {
   uint64_t *ptr = nullptr;    // n+1
   uint32_t *col = nullptr;    // m
   uint32_t *order = nullptr;  // n, roots by out-degree descending
+  uint64_t *key = nullptr;    // n, the ranking key: v precedes w iff (key[v], v) < (key[w], w)
   std::vector<uint64_t> ge;   // ge[t] = #roots with out-degree >= t, t = 0 .. max_out+1
   cudaStream_t stream = nullptr;
   int device = 0;

@@ -137,6 +137,12 @@ struct CountArgs {
   uint32_t light_by_id;
   uint32_t n;
   uint32_t light_min, light_max;
+  // peeling: root q's candidate row is rcol[rptr[q] .. rptr[q+1]) (sorted
+  // by rank) and its vertex is rvert[q]; order[] then lists row indices.
+  // Members' rows are still the DAG's. Null: roots are vertices.
+  const uint64_t *rptr;
+  const uint32_t *rcol;
+  const uint32_t *rvert;
 };
 
 // A configured counting pass (kc_api.cu).

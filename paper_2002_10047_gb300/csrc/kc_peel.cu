@@ -1,0 +1,285 @@
+// arb-peel (Algorithm 2, Section 4.1): exact k-clique densest-subgraph
+// peeling, seeded by the per-vertex counts of arb-count-v.
+//
+// Every round peels all live vertices of minimum current k-clique count (the
+// set A). Update recounts only what A removes: for each v in A it counts the
+// (k-1)-cliques of I(v) = {live neighbours of v} plus {neighbours of v in A
+// ranked after v}, so a clique holding several members of A is counted once,
+// at its lowest-ranked member of A. Those counts run on the same persistent
+// counting kernels as arb-count, with v as the root and I(v), sorted by rank,
+// as its candidate row; the per-vertex credits of that pass are subtracted
+// from the live members' counts. The density of what remains after each
+// round is compared exactly, as a fraction, with the best so far.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kc_host.cuh"
+#include "kc_orient.cuh"
+
+namespace kc {
+namespace {
+
+constexpr uint32_t kAlive = 0xffffffffu;
+constexpr int kPeelBlock = 256;
+
+__device__ __forceinline__ bool rank_lt(uint64_t ka, uint32_t a, uint64_t kb, uint32_t b) {
+  return ka < kb || (ka == kb && a < b);
+}
+
+// smallest current count among live vertices
+__global__ void peel_min_kernel(const unsigned long long *__restrict__ C, const uint32_t *__restrict__ round,
+                                uint32_t n, unsigned long long *minv) {
+  unsigned long long m = ~0ull;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+    if (round[v] == kAlive && C[v] < m) m = C[v];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y < m ? y : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m != ~0ull) atomicMin(minv, m);
+}
+
+// A = live vertices with the minimum count; they get this round's index
+__global__ void peel_mark_kernel(const unsigned long long *__restrict__ C, uint32_t *__restrict__ round, uint32_t n,
+                                 const unsigned long long *minv, uint32_t r, uint32_t *__restrict__ A,
+                                 unsigned *nA) {
+  const unsigned long long mv = *minv;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+    if (round[v] == kAlive && C[v] == mv) {
+      round[v] = r;
+      A[atomicAdd(nA, 1u)] = (uint32_t)v;
+    }
+}
+
+__device__ __forceinline__ bool in_I(uint32_t u, uint32_t v, uint64_t kv, const uint32_t *round, const uint64_t *key,
+                                     uint32_t r) {
+  const uint32_t ru = round[u];
+  return ru == kAlive || (ru == r && rank_lt(kv, v, key[u], u));
+}
+
+// |I(v)| for every v in A (one warp per member of A)
+__global__ void peel_len_kernel(const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                                const uint64_t *__restrict__ key, const uint32_t *__restrict__ round,
+                                const uint32_t *__restrict__ A, uint32_t nA, uint32_t r, uint32_t *__restrict__ len,
+                                unsigned *maxlen) {
+  const unsigned lane = threadIdx.x & 31;
+  const size_t w0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+  const size_t nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t q = w0; q < nA; q += nw) {
+    const uint32_t v = A[q];
+    const uint64_t kv = key[v], e1 = rp[v + 1];
+    unsigned c = 0;
+    for (uint64_t e = rp[v] + lane; e < e1; e += 32) c += in_I(col[e], v, kv, round, key, r) ? 1u : 0u;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) {
+      len[q] = c;
+      atomicMax(maxlen, c);
+    }
+  }
+}
+
+// the rows I(v) (in the CSR's id order; sorted by rank afterwards)
+__global__ void peel_fill_kernel(const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                                 const uint64_t *__restrict__ key, const uint32_t *__restrict__ round,
+                                 const uint32_t *__restrict__ A, uint32_t nA, uint32_t r,
+                                 const uint64_t *__restrict__ rptr, uint32_t *__restrict__ rcol) {
+  const unsigned lane = threadIdx.x & 31;
+  const size_t w0 = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+  const size_t nw = ((size_t)gridDim.x * blockDim.x) >> 5;
+  for (size_t q = w0; q < nA; q += nw) {
+    const uint32_t v = A[q];
+    const uint64_t kv = key[v], e0 = rp[v], e1 = rp[v + 1];
+    uint64_t out = rptr[q];
+    const uint64_t end = rptr[q + 1];
+    for (uint64_t b = e0; b < e1; b += 32) {  // warp-uniform trip count
+      const uint64_t e = b + lane;
+      uint32_t u = 0;
+      bool inc = false;
+      if (e < e1) {
+        u = col[e];
+        inc = in_I(u, v, kv, round, key, r);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, inc);
+      const uint64_t at = out + (unsigned)__popc(m & ((1u << lane) - 1u));
+      if (inc && at < end) rcol[at] = u;
+      out += (unsigned)__popc(m);
+    }
+  }
+}
+
+// subtract the credits of this round from the live vertices' counts and
+// clear the credit array where it was written (each entry is taken once)
+__global__ void peel_apply_kernel(unsigned long long *__restrict__ C, unsigned long long *__restrict__ dec,
+                                  const uint32_t *__restrict__ round, const uint32_t *__restrict__ rcol, uint64_t nr,
+                                  const uint32_t *__restrict__ A, uint32_t nA, unsigned *status) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nr + nA; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t x = i < nr ? rcol[i] : A[i - nr];
+    const unsigned long long val = atomicExch(&dec[x], 0ull);
+    if (val && round[x] == kAlive) {
+      if (val > C[x]) {
+        atomicOr(status, ST_CAPACITY);  // counts inconsistent: cannot happen with exact counts
+        continue;
+      }
+      C[x] -= val;
+    }
+  }
+}
+
+unsigned grid_for(size_t work, int block) {
+  size_t g = (work + block - 1) / block;
+  g = std::max<size_t>(1, std::min<size_t>(g, (size_t)sm_count() * 32));
+  return (unsigned)g;
+}
+
+// 128-bit a*b > c*d for the density comparison
+bool frac_gt(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+  return (unsigned __int128)a * b > (unsigned __int128)c * d;
+}
+
+}  // namespace
+}  // namespace kc
+
+extern "C" kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *d_round, kc_peel_result *out,
+                             kc_stream_t stream) {
+  using namespace kc;
+  if (!g || !d || !out || k < 3 || k > KC_KMAX) return KC_EINVAL;
+  if (g->n != d->n || g->nnz != 2 * d->m) return KC_EINVAL;
+  const uint32_t n = d->n;
+  memset(out, 0, sizeof *out);
+  if (n == 0) return KC_OK;
+  if (!d_round || !g->d_row_ptr || !d->key) return KC_EINVAL;
+  if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  DevBuf C, dec, A, len, rptr, rcol, scan_tmp, work, rorder;
+  KC_CK(C.alloc(sizeof(unsigned long long) * n, s));
+  KC_CK(dec.alloc(sizeof(unsigned long long) * n, s));
+  KC_CK(A.alloc(sizeof(uint32_t) * n, s));
+  KC_CK(len.alloc(sizeof(uint32_t) * n, s));
+  KC_CK(rptr.alloc(sizeof(uint64_t) * ((size_t)n + 1), s));
+  KC_CK(rcol.alloc(sizeof(uint32_t) * std::max<uint64_t>(g->nnz, 1), s));
+  KC_CK(rorder.alloc(sizeof(uint32_t) * n, s));
+  const size_t te = scan_tmp_elems(n);
+  KC_CK(scan_tmp.alloc(sizeof(uint64_t) * te, s));
+  KC_CK(work.alloc(64, s));  // min @0, |A| @8, max |I| @12, status @16
+  uint8_t *w = work.as<uint8_t>();
+  unsigned long long *d_min = (unsigned long long *)w;
+  unsigned *d_nA = (unsigned *)(w + 8), *d_maxlen = (unsigned *)(w + 12), *d_status = (unsigned *)(w + 16);
+  KC_CK(cudaMemsetAsync(dec.p, 0, sizeof(unsigned long long) * n, s));
+  KC_CK(cudaMemsetAsync(d_round, 0xff, sizeof(uint32_t) * n, s));
+  KC_CK(cudaMemsetAsync(w + 16, 0, 4, s));
+
+  // the seed: per-vertex counts of the whole graph (arb-count-v)
+  uint64_t total = 0;
+  kc_status st = run_count(d, k, C.as<unsigned long long>(), nullptr, &total, 0, s);
+  if (st != KC_OK) return st;
+
+  uint64_t t_rem = total, f = 0;
+  uint64_t best_num = total, best_den = n;
+  uint32_t best_rounds = 0, r = 0;
+  while (f < n) {
+    KC_CK(cudaMemsetAsync(d_min, 0xff, 8, s));
+    KC_CK(cudaMemsetAsync(w + 8, 0, 8, s));
+    peel_min_kernel<<<grid_for(n, kPeelBlock), kPeelBlock, 0, s>>>(C.as<unsigned long long>(), d_round, n, d_min);
+    note_launch();
+    peel_mark_kernel<<<grid_for(n, kPeelBlock), kPeelBlock, 0, s>>>(C.as<unsigned long long>(), d_round, n, d_min, r,
+                                                                    A.as<uint32_t>(), d_nA);
+    note_launch();
+    unsigned h_nA = 0;
+    KC_CK(cudaMemcpyAsync(&h_nA, d_nA, 4, cudaMemcpyDeviceToHost, s));
+    KC_CK(cudaStreamSynchronize(s));
+    if (h_nA == 0) return KC_ECUDA;  // no live vertex found although f < n: cannot happen
+    f += h_nA;
+    if (t_rem > 0) {
+      // Update (Algorithm 2): the k-cliques that A removes
+      peel_len_kernel<<<grid_for((size_t)h_nA * 32, kPeelBlock), kPeelBlock, 0, s>>>(
+          g->d_row_ptr, g->d_col, d->key, d_round, A.as<uint32_t>(), h_nA, r, len.as<uint32_t>(), d_maxlen);
+      note_launch();
+      KC_CK(exclusive_scan_u32(len.as<uint32_t>(), rptr.as<uint64_t>(), h_nA, scan_tmp.as<uint64_t>(), te, s));
+      uint64_t h_nr = 0;
+      unsigned h_maxlen = 0;
+      KC_CK(cudaMemcpyAsync(&h_nr, rptr.as<uint64_t>() + h_nA, 8, cudaMemcpyDeviceToHost, s));
+      KC_CK(cudaMemcpyAsync(&h_maxlen, d_maxlen, 4, cudaMemcpyDeviceToHost, s));
+      KC_CK(cudaStreamSynchronize(s));
+      if (h_nr > g->nnz) return KC_ECUDA;
+      if (h_maxlen + 1 >= (unsigned)k && h_nr > 0) {
+        if (h_maxlen > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
+        peel_fill_kernel<<<grid_for((size_t)h_nA * 32, kPeelBlock), kPeelBlock, 0, s>>>(
+            g->d_row_ptr, g->d_col, d->key, d_round, A.as<uint32_t>(), h_nA, r, rptr.as<uint64_t>(),
+            rcol.as<uint32_t>());
+        note_launch();
+        // rows by length, descending (the counting kernels' root order), then
+        // each row into rank order
+        DevBuf hist;
+        KC_CK(hist.alloc(sizeof(unsigned) * ((size_t)h_maxlen + 1), s));
+        KC_CK(cudaMemsetAsync(hist.p, 0, sizeof(unsigned) * ((size_t)h_maxlen + 1), s));
+        KC_CK(launch_outdeg_hist(rptr.as<uint64_t>(), h_nA, hist.as<unsigned>(), h_maxlen, s));
+        std::vector<unsigned> h_hist((size_t)h_maxlen + 1);
+        KC_CK(cudaMemcpyAsync(h_hist.data(), hist.p, sizeof(unsigned) * h_hist.size(), cudaMemcpyDeviceToHost, s));
+        KC_CK(cudaStreamSynchronize(s));
+        kc_dag rows;  // the round's rows in the shape the planner reads
+        rows.n = n;
+        rows.m = h_nr;
+        rows.max_out = h_maxlen;
+        rows.ptr = d->ptr;
+        rows.col = d->col;
+        rows.order = rorder.as<uint32_t>();
+        rows.ge.assign((size_t)h_maxlen + 2, 0);
+        for (int64_t t = h_maxlen; t >= 0; --t) rows.ge[t] = rows.ge[t + 1] + h_hist[t];
+        std::vector<unsigned> start((size_t)h_maxlen + 1);
+        for (uint32_t t = 0; t <= h_maxlen; ++t) start[t] = (unsigned)rows.ge[t + 1];
+        KC_CK(cudaMemcpyAsync(hist.p, start.data(), sizeof(unsigned) * start.size(), cudaMemcpyHostToDevice, s));
+        KC_CK(launch_outdeg_scatter(rptr.as<uint64_t>(), h_nA, hist.as<unsigned>(), h_maxlen, rorder.as<uint32_t>(), s));
+        auto ge = [&](uint64_t t) -> uint32_t { return t < rows.ge.size() ? (uint32_t)rows.ge[t] : 0u; };
+        KC_CK(launch_sort_rows(rptr.as<uint64_t>(), rcol.as<uint32_t>(), d->key, rorder.as<uint32_t>(), ge(1025), ge(33),
+                               ge(2), h_maxlen, s));
+        LaunchPlan P;
+        KC_CK(plan_count(&rows, k, true, false, nullptr, &P));
+        CountArgs &a = P.a;
+        a.rptr = rptr.as<uint64_t>();
+        a.rcol = rcol.as<uint32_t>();
+        a.rvert = A.as<uint32_t>();
+        a.pv = dec.as<unsigned long long>();
+        DevBuf cwork, scratch;
+        KC_CK(cwork.alloc(kc_work_bytes(), s));
+        KC_CK(cudaMemsetAsync(cwork.p, 0, kc_work_bytes(), s));
+        set_work(&a, cwork.as<uint8_t>());
+        if (P.scratch_bytes) {
+          KC_CK(scratch.alloc(P.scratch_bytes, s));
+          a.scratch = scratch.as<uint8_t>();
+        }
+        if (a.n_light_end > 0) KC_CK(launch_count(a, true, false, P.block_grid, P.warp_grid, P.block_smem, s));
+        peel_apply_kernel<<<grid_for(h_nr + h_nA, kPeelBlock), kPeelBlock, 0, s>>>(
+            C.as<unsigned long long>(), dec.as<unsigned long long>(), d_round, rcol.as<uint32_t>(), h_nr,
+            A.as<uint32_t>(), h_nA, d_status);
+        note_launch();
+        unsigned long long h[2] = {0, 0};
+        unsigned h_st = 0;
+        KC_CK(cudaMemcpyAsync(h, cwork.p, sizeof h, cudaMemcpyDeviceToHost, s));
+        KC_CK(cudaMemcpyAsync(&h_st, d_status, 4, cudaMemcpyDeviceToHost, s));
+        KC_CK(cudaStreamSynchronize(s));  // also orders the pageable `start` copy
+        const kc_status cs = status_code((unsigned)h[1] | h_st);
+        if (cs != KC_OK) return cs;
+        if (h[0] > t_rem) return KC_ECUDA;  // removed more cliques than remain: cannot happen
+        t_rem -= h[0];
+      }
+    }
+    if (f < n && frac_gt(t_rem, best_den, best_num, n - f)) {
+      best_num = t_rem;
+      best_den = n - f;
+      best_rounds = r + 1;
+    }
+    ++r;
+  }
+  out->rounds = r;
+  out->best_rounds = best_rounds;
+  out->best_cliques = best_num;
+  out->best_vertices = best_den;
+  out->total = total;
+  return KC_OK;
+}

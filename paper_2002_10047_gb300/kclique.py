@@ -73,6 +73,11 @@ class _ServerStats(ctypes.Structure):
                                                 "peak_bytes", "bytes_in_use", "queued")]
 
 
+class _PeelResult(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint32), ("best_rounds", ctypes.c_uint32), ("best_cliques", ctypes.c_uint64),
+                ("best_vertices", ctypes.c_uint64), ("total", ctypes.c_uint64)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("sum_out_sq", ctypes.c_uint64), ("sum_arc_head", ctypes.c_uint64),
                 ("triangles", ctypes.c_uint64), ("max_out", ctypes.c_uint32)]
@@ -129,6 +134,8 @@ def _load():
         for f in (lib.kc_server_create, lib.kc_server_submit, lib.kc_server_wait, lib.kc_server_fetch_per_vertex,
                   lib.kc_server_release, lib.kc_server_get_stats):
             f.restype = I
+        lib.kc_peel.argtypes = [ctypes.POINTER(_Csr), P, I, P, ctypes.POINTER(_PeelResult), P]
+        lib.kc_peel.restype = I
         lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         lib.kc_measure_word_op_rate.restype = I
         lib.kc_kernel_launches.argtypes = []
@@ -405,6 +412,24 @@ class Server:
             pass
 
 
+def kc_peel(row_ptr: torch.Tensor, col: torch.Tensor, dag: Dag, k: int, out: torch.Tensor | None = None,
+            stream=None):
+    """arb-peel: (result dict, rounds int32[n]) for the CSR the DAG was oriented from.
+
+    result: rounds, best_rounds, best_cliques, best_vertices (the best density
+    is best_cliques / best_vertices, exactly), total."""
+    _require_cuda(row_ptr, "row_ptr", (torch.int64,))
+    _require_cuda(col, "col", (torch.int32,))
+    n = row_ptr.numel() - 1
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=row_ptr.device)
+    _require_cuda(out, "out", (torch.int32,))
+    g = _Csr(n, col.numel(), row_ptr.data_ptr(), col.data_ptr() if col.numel() else 0)
+    res = _PeelResult()
+    _check(_load().kc_peel(ctypes.byref(g), dag.handle, int(k), out.data_ptr(), ctypes.byref(res), _stream(stream)))
+    return ({f: int(getattr(res, f)) for f, _ in _PeelResult._fields_}, out[:n])
+
+
 def kc_dag_get_stats(dag: Dag, stream=None) -> dict:
     st = _Stats()
     _check(_load().kc_dag_get_stats(dag.handle, ctypes.byref(st), _stream(stream)))
@@ -430,6 +455,7 @@ count = kc_count
 count_per_vertex = kc_count_per_vertex
 count_per_arc = kc_count_per_arc
 count_batched = kc_count_batched
+peel = kc_peel
 autotune_batched = kc_autotune_batched
 dag_stats = kc_dag_get_stats
 
