@@ -48,10 +48,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--json-out", default=None)
-    ap.add_argument("--workload", choices=["rmat", "batch", "serve", "chunglu"], default="rmat",
+    ap.add_argument("--workload", choices=["rmat", "batch", "serve", "chunglu", "peel"], default="rmat",
                     help="rmat: one large graph, k = --ks; batch: the 4096-graph mixed batch; "
                          "serve: Poisson request stream on a pool of resident graphs; "
-                         "chunglu: 50M-vertex Chung-Lu with planted cliques, k = 4")
+                         "chunglu: 50M-vertex Chung-Lu with planted cliques, k = 4; "
+                         "peel: arb-peel (Algorithm 2) on R-MAT, k = --peel-k")
+    ap.add_argument("--peel-scale", type=int, default=16)
+    ap.add_argument("--peel-k", type=int, default=4)
     ap.add_argument("--rates", default="10,30,100,300", help="serve: arrival rates swept (req/s)")
     ap.add_argument("--requests", type=int, default=400, help="serve: requests per rate")
     ap.add_argument("--pool-max-scale", type=int, default=12)
@@ -1211,20 +1214,133 @@ def run_chunglu(args, rank, world):
             f.write(out + "\n")
 
 
+# ------------------------------------------------------------- peeling workload
+PEEL_METRIC = "vertices peeled/sec (arb-peel)"
+PEEL_UNIT = "vertices/s"
+
+
+def peel_workload(args) -> str:
+    return (f"arb-peel (Algorithm 2), k={args.peel_k}, on R-MAT scale {args.peel_scale}, edge factor 16, "
+            "(a,b,c,d)=(0.57,0.19,0.19,0.05), seed 2, ids permuted; seeded by arb-count-v; degree order")
+
+
+def oracle_peel_rate(g, k: int, seconds: float):
+    """The oracle's peel (counts recomputed on the remaining graph every round)
+    on the same graph, stopped after the round that passes the budget."""
+    import oracle
+    n = g.n
+    keep = np.ones(n, dtype=bool)
+    t0 = time.perf_counter()
+    done, rounds = 0, 0
+    while keep.any() and time.perf_counter() - t0 < seconds:
+        sub, ids = oracle._induced(g, keep)
+        _, pv = oracle.count_per_vertex(oracle.orient(sub, "degree"), k)
+        peel_now = ids[pv == pv.min()]
+        keep[peel_now] = False
+        done += peel_now.size
+        rounds += 1
+    dt = time.perf_counter() - t0
+    return done / dt, done, rounds, dt
+
+
+def run_reference_peel(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2002_10047_gb300 import graphgen as gg
+    g = gg.rmat(args.peel_scale, 16, 0.57, 0.19, 0.19, seed=2, permute=True)
+    cores = host_cores()
+    budget = max(2.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    rates, desc = [], ""
+    for i in range(args.warmup + args.steps):
+        r, done, rounds, dt = oracle_peel_rate(g, args.peel_k, budget)
+        desc = f"the first {rounds} rounds ({done} of {g.n} vertices) in {dt:.1f} s"
+        if i >= args.warmup:
+            rates.append(r)
+    v = statistics.median(rates)
+    line = {"impl": "reference", "metric": PEEL_METRIC, "value": v, "unit": PEEL_UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": peel_workload(args)},
+            "cpu_baseline": {"value": v, "unit": PEEL_UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {desc}"},
+            "e2e": {"value": v, "unit": PEEL_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_peel(args, rank, world):
+    import torch
+
+    from paper_2002_10047_gb300 import build as kbuild
+    kbuild.build()
+    from paper_2002_10047_gb300 import graphgen as gg
+    from paper_2002_10047_gb300 import kclique as kc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    g = gg.rmat(args.peel_scale, 16, 0.57, 0.19, 0.19, seed=2, permute=True)
+    rp, col = kc.csr_to_device(g, dev)
+    rounds_buf = torch.empty(g.n, dtype=torch.int32, device=dev)
+
+    def step():
+        dag = kc.orient(rp, col, g.n, method="degree")
+        res, _ = kc.peel(rp, col, dag, args.peel_k, out=rounds_buf)
+        dag.free()
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res2 = step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            assert res2 == res
+    t = sum(ms) / len(ms)
+    t_max = max_over_ranks(t, world, dev)
+    if rank != 0:
+        return
+    line = {
+        "metric": PEEL_METRIC, "value": whole_job_rate(g.n, world, t_max), "unit": PEEL_UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": peel_workload(args), "n": g.n, "m": g.m, "k": args.peel_k},
+        "peel": res, "best_density": res["best_cliques"] / max(1, res["best_vertices"]),
+        "rounds_per_s": res["rounds"] / (t_max / 1e3), "clocks": clk.summary(),
+        "note": "one host synchronisation per round (the next round's set depends on this round's counts)",
+    }
+    if not args.no_cpu_baseline:
+        r, done, rounds, dt = oracle_peel_rate(g, args.peel_k, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": PEEL_UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the first {rounds} rounds ({done} of {g.n} vertices) in {dt:.1f} s"}
+    out = json.dumps(line)
+    print(out, flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(out + "\n")
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
-        {"batch": run_reference_batch, "serve": run_reference_serve,
-         "chunglu": run_reference_chunglu}.get(args.workload, run_reference)(
+        {"batch": run_reference_batch, "serve": run_reference_serve, "chunglu": run_reference_chunglu,
+         "peel": run_reference_peel}.get(args.workload, run_reference)(
             args, rank, world)
         return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        {"batch": run_batch, "serve": run_serve, "chunglu": run_chunglu}.get(args.workload, run_ours)(
+        {"batch": run_batch, "serve": run_serve, "chunglu": run_chunglu, "peel": run_peel}.get(
+            args.workload, run_ours)(
             args, rank, world)
     finally:
         if world > 1:
