@@ -3,6 +3,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <utility>
+
 #include "kc_internal.cuh"
 
 namespace kc {
@@ -31,10 +36,32 @@ uint32_t block_root_capacity(size_t smem_budget, bool pv, bool pa) {
 }
 
 cudaError_t count_occupancy(bool pv, bool pa, size_t block_smem, int *block_per_sm, int *warp_per_sm) {
-  if (pv) return pa ? occupancy_variant<true, true>(block_smem, block_per_sm, warp_per_sm)
-                    : occupancy_variant<true, false>(block_smem, block_per_sm, warp_per_sm);
-  return pa ? occupancy_variant<false, true>(block_smem, block_per_sm, warp_per_sm)
-            : occupancy_variant<false, false>(block_smem, block_per_sm, warp_per_sm);
+  // the answer depends only on (device, variant, shared-memory size): cached,
+  // since repeated passes (peeling rounds, served requests) ask again and again
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, size_t>, std::pair<int, int>> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const auto key = std::make_tuple(dev, (pv ? 2 : 0) | (pa ? 1 : 0), block_smem);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *block_per_sm = it->second.first;
+      *warp_per_sm = it->second.second;
+      return cudaSuccess;
+    }
+  }
+  if (pv) e = pa ? occupancy_variant<true, true>(block_smem, block_per_sm, warp_per_sm)
+                 : occupancy_variant<true, false>(block_smem, block_per_sm, warp_per_sm);
+  else e = pa ? occupancy_variant<false, true>(block_smem, block_per_sm, warp_per_sm)
+              : occupancy_variant<false, false>(block_smem, block_per_sm, warp_per_sm);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = std::make_pair(*block_per_sm, *warp_per_sm);
+  }
+  return e;
 }
 
 cudaError_t launch_count(const CountArgs &a, bool pv, bool pa, int block_grid, int warp_grid, size_t block_smem,

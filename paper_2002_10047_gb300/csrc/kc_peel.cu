@@ -30,6 +30,15 @@ __device__ __forceinline__ bool rank_lt(uint64_t ka, uint32_t a, uint64_t kb, ui
   return ka < kb || (ka == kb && a < b);
 }
 
+// largest row length of a CSR
+__global__ void row_len_max_kernel(const uint64_t *__restrict__ rp, uint32_t n, unsigned *out) {
+  unsigned m = 0;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned)(rp[v + 1] - rp[v]));
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
 // smallest current count among live vertices
 __global__ void peel_min_kernel(const unsigned long long *__restrict__ C, const uint32_t *__restrict__ round,
                                 uint32_t n, unsigned long long *minv) {
@@ -167,6 +176,24 @@ extern "C" kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *
   const size_t te = scan_tmp_elems(n);
   KC_CK(scan_tmp.alloc(sizeof(uint64_t) * te, s));
   KC_CK(work.alloc(64, s));  // min @0, |A| @8, max |I| @12, status @16
+  // per-round buffers, sized once: the length histogram (|I(v)| <= the
+  // largest degree), the counting pass's work block, and global scratch
+  // grown on demand for rows too long for shared memory
+  uint32_t maxdeg = 0;
+  {
+    DevBuf dmax;
+    KC_CK(dmax.alloc(sizeof(unsigned), s));
+    KC_CK(cudaMemsetAsync(dmax.p, 0, sizeof(unsigned), s));
+    row_len_max_kernel<<<grid_for(n, kPeelBlock), kPeelBlock, 0, s>>>(g->d_row_ptr, n, dmax.as<unsigned>());
+    note_launch();
+    KC_CK(cudaGetLastError());
+    KC_CK(cudaMemcpyAsync(&maxdeg, dmax.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    KC_CK(cudaStreamSynchronize(s));
+  }
+  DevBuf hist, cwork, scratch;
+  size_t scratch_cap = 0;
+  KC_CK(hist.alloc(sizeof(unsigned) * ((size_t)maxdeg + 1), s));
+  KC_CK(cwork.alloc(kc_work_bytes(), s));
   uint8_t *w = work.as<uint8_t>();
   unsigned long long *d_min = (unsigned long long *)w;
   unsigned *d_nA = (unsigned *)(w + 8), *d_maxlen = (unsigned *)(w + 12), *d_status = (unsigned *)(w + 16);
@@ -215,8 +242,7 @@ extern "C" kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *
         note_launch();
         // rows by length, descending (the counting kernels' root order), then
         // each row into rank order
-        DevBuf hist;
-        KC_CK(hist.alloc(sizeof(unsigned) * ((size_t)h_maxlen + 1), s));
+        if (h_maxlen > maxdeg) return KC_ECUDA;  // |I(v)| <= deg(v): cannot happen
         KC_CK(cudaMemsetAsync(hist.p, 0, sizeof(unsigned) * ((size_t)h_maxlen + 1), s));
         KC_CK(launch_outdeg_hist(rptr.as<uint64_t>(), h_nA, hist.as<unsigned>(), h_maxlen, s));
         std::vector<unsigned> h_hist((size_t)h_maxlen + 1);
@@ -245,12 +271,14 @@ extern "C" kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *
         a.rcol = rcol.as<uint32_t>();
         a.rvert = A.as<uint32_t>();
         a.pv = dec.as<unsigned long long>();
-        DevBuf cwork, scratch;
-        KC_CK(cwork.alloc(kc_work_bytes(), s));
         KC_CK(cudaMemsetAsync(cwork.p, 0, kc_work_bytes(), s));
         set_work(&a, cwork.as<uint8_t>());
         if (P.scratch_bytes) {
-          KC_CK(scratch.alloc(P.scratch_bytes, s));
+          if (P.scratch_bytes > scratch_cap) {
+            if (scratch.p) cudaFreeAsync(scratch.release(), s);
+            KC_CK(scratch.alloc(P.scratch_bytes, s));
+            scratch_cap = P.scratch_bytes;
+          }
           a.scratch = scratch.as<uint8_t>();
         }
         if (a.n_light_end > 0) KC_CK(launch_count(a, true, false, P.block_grid, P.warp_grid, P.block_smem, s));
