@@ -48,11 +48,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--json-out", default=None)
-    ap.add_argument("--workload", choices=["rmat", "batch", "serve", "chunglu", "peel"], default="rmat",
+    ap.add_argument("--workload", choices=["rmat", "batch", "serve", "chunglu", "peel", "colorful"], default="rmat",
                     help="rmat: one large graph, k = --ks; batch: the 4096-graph mixed batch; "
                          "serve: Poisson request stream on a pool of resident graphs; "
                          "chunglu: 50M-vertex Chung-Lu with planted cliques, k = 4; "
-                         "peel: arb-peel (Algorithm 2) on R-MAT, k = --peel-k")
+                         "peel: arb-peel (Algorithm 2) on R-MAT, k = --peel-k; "
+                         "colorful: approximate counts by colorful sparsification on R-MAT scale 20, k = 6")
     ap.add_argument("--peel-scale", type=int, default=16)
     ap.add_argument("--peel-k", type=int, default=4)
     ap.add_argument("--rates", default="10,30,100,300", help="serve: arrival rates swept (req/s)")
@@ -451,7 +452,7 @@ def run_ours(args, rank, world):
     st = kc.dag_stats(dag)
     m = dag.m
     dag.free()
-    # algorithmic bytes of one counting pass (first-level induced subgraphs, Section 3.3):
+    # algorithmic bytes of one counting pass (first-level induced subgraphs, Section 3.4):
     # root offsets + root list + out-neighbour offsets + out-neighbour lists + per-vertex output
     b_count = 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * st["sum_arc_head"] + 8 * n
     # algorithmic integer work of one pass: one bitset intersect (64-bit AND +
@@ -1326,21 +1327,113 @@ def run_peel(args, rank, world):
             f.write(out + "\n")
 
 
+# ------------------------------------------------------------- colorful sparsification
+COLOR_METRIC = "approximate k-cliques/sec (colorful sparsification)"
+COLOR_K, COLOR_C = 6, 4
+
+
+def colorful_workload() -> str:
+    return (f"colorful sparsification (Section 3.3), {COLOR_C} colors, k={COLOR_K}, on R-MAT scale 20, edge "
+            "factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 2; color + filter + orient + exact count of the "
+            "monochromatic graph; estimate = count * colors^(k-1)")
+
+
+def run_reference_colorful(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    g = make_graph(args.scale)
+    rates, desc = [], ""
+    budget = max(2.0, min(args.cpu_seconds, 60.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        c, est = oracle.colorful_count(g, COLOR_K, COLOR_C, 1000 + i)
+        dt = time.perf_counter() - t0
+        rates.append(est / dt)
+        desc = f"one full oracle run ({dt:.1f} s, single thread)"
+        if dt > budget:
+            break
+    v = statistics.median(rates[-max(1, args.steps):])
+    line = {"impl": "reference", "metric": COLOR_METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": colorful_workload()},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_colorful(args, rank, world):
+    import torch
+
+    from paper_2002_10047_gb300 import build as kbuild
+    kbuild.build()
+    from paper_2002_10047_gb300 import kclique as kc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    g = make_graph(args.scale)
+    rp, col = kc.csr_to_device(g, dev)
+    dag = kc.orient(rp, col, g.n)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    exact = kc.count(dag, COLOR_K)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_exact = a.elapsed_time(b)
+    dag.free()
+    for i in range(args.warmup):
+        kc.count_colorful(rp, col, COLOR_K, COLOR_C, 1000 + i)
+    ms, ests = [], []
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, est = kc.count_colorful(rp, col, COLOR_K, COLOR_C, 2000 + i)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            ests.append(est)
+    t = sum(ms) / len(ms)
+    t_max = max_over_ranks(t, world, dev)
+    if rank != 0:
+        return
+    errs = [abs(e - exact) / exact for e in ests]
+    line = {
+        "metric": COLOR_METRIC, "value": whole_job_rate(float(np.mean(ests)), world, t_max), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": colorful_workload(), "seeds": f"2000..{2000 + args.steps - 1}"},
+        "exact": {"cliques": exact, "ms": t_exact}, "speedup_vs_exact": t_exact / t,
+        "relative_error": {"mean": float(np.mean(errs)), "max": float(np.max(errs))},
+        "estimates": ests, "clocks": clk.summary(),
+    }
+    out = json.dumps(line)
+    print(out, flush=True)
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            f.write(out + "\n")
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         {"batch": run_reference_batch, "serve": run_reference_serve, "chunglu": run_reference_chunglu,
-         "peel": run_reference_peel}.get(args.workload, run_reference)(
+         "peel": run_reference_peel, "colorful": run_reference_colorful}.get(args.workload, run_reference)(
             args, rank, world)
         return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     try:
-        {"batch": run_batch, "serve": run_serve, "chunglu": run_chunglu, "peel": run_peel}.get(
-            args.workload, run_ours)(
+        {"batch": run_batch, "serve": run_serve, "chunglu": run_chunglu, "peel": run_peel,
+         "colorful": run_colorful}.get(args.workload, run_ours)(
             args, rank, world)
     finally:
         if world > 1:

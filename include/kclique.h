@@ -331,6 +331,25 @@ kc_status kc_server_get_stats(kc_server *s, kc_server_stats *out);
 void kc_server_destroy(kc_server *s);
 
 /*
+ * kc_count_colorful -- approximate k-clique count by colorful sparsification
+ * (Section 3.3, "Sampling"; estimator theorem in Appendix B): every vertex
+ * takes a color in [0, colors) uniformly at random, only monochromatic edges
+ * are kept, and the k-clique count C of that graph (oriented by `method`,
+ * counted exactly by arb-count) gives the unbiased estimate C * colors^(k-1).
+ *   g                the input CSR (validated as by kc_orient)
+ *   k                1 .. KC_KMAX
+ *   colors           c >= 1 (c = 1 keeps every edge: the exact count)
+ *   seed             vertex v's color is the high 32 bits of
+ *                    splitmix64(seed + (v + 1) * 0x9E3779B97F4A7C15)
+ *                    (Steele, Lea and Flood, 2014) scaled to [0, c)
+ *   h_sparse_count   receives C (exact)
+ *   h_estimate       optional: receives C * c^(k-1) (double)
+ * Synchronises `stream`.
+ */
+kc_status kc_count_colorful(const kc_csr *g, int k, uint32_t colors, uint64_t seed, int method,
+                            uint64_t *h_sparse_count, double *h_estimate, kc_stream_t stream);
+
+/*
  * kc_peel -- arb-peel (Algorithm 2, Section 4.1): exact k-clique peeling for
  * the k-clique densest subgraph, seeded by arb-count-v. Each round removes
  * every remaining vertex whose current k-clique count (in the graph induced
@@ -368,7 +387,7 @@ kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *d_round, kc
  * must move (computed exactly on the device):
  *   sum_out_sq     sum over roots u of d+(u)^2
  *   sum_arc_head   sum over arcs u->v of d+(v) (adjacency read to build the
- *                  first-level induced subgraphs of Section 3.3)
+ *                  first-level induced subgraphs of Section 3.4)
  *   triangles      number of 3-cliques
  *   max_out        largest out-degree
  */

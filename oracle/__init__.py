@@ -14,6 +14,11 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   cliques, and the 4-clique fragment of the paper's worked example
   (Appendix A, Figure 7; the figure itself is missing, so that pin is partial).
 * ``count_arc``: sums over all arcs equal ``count`` (k >= 2).
+* ``colorful_count`` (colorful sparsification, Section 3.3): one color gives
+  the exact count; over many seeds the estimate's mean and variance match
+  the appendix theorem (E[Y] = X, Var[Y] from the counts s_z of clique pairs
+  sharing z vertices, computed by brute force); the color generator gives
+  splitmix64's well-known first output for seed 0 (0xe220a8397b1dcdaf).
 * ``peel`` (arb-peel, Algorithm 2): K_n in one round at C(n,k)/n; a disjoint
   K_a + K_b in two rounds at C(b,k)/b; no k-clique -> one round at 0; the
   1/k guarantee against a brute-force densest subset (n <= 12); peeling
@@ -342,3 +347,40 @@ def peel(g, k: int):
     if total is None:
         total, best = 0, (0, 0, 0)
     return PeelResult(r, best[2], best[0], best[1], total), rounds
+
+
+_MASK64 = (1 << 64) - 1
+
+
+def splitmix64(state: int) -> int:
+    """splitmix64 output for a given state (Steele, Lea and Flood, 2014)."""
+    z = state & _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def vertex_colors(n: int, colors: int, seed: int) -> np.ndarray:
+    """Color of every vertex: splitmix64(seed + (v + 1) * gamma), high 32 bits
+    scaled to [0, colors)."""
+    gamma = 0x9E3779B97F4A7C15
+    out = np.empty(n, dtype=np.int64)
+    for v in range(n):
+        z = splitmix64((seed + (v + 1) * gamma) & _MASK64)
+        out[v] = ((z >> 32) * colors) >> 32
+    return out
+
+
+def colorful_count(g, k: int, colors: int, seed: int):
+    """Colorful sparsification (Section 3.3): keep the edges whose endpoints
+    share a color, count k-cliques exactly. Returns (C, C * colors^(k-1))."""
+    col = vertex_colors(g.n, colors, seed)
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr.astype(np.int64)))
+    dst = g.col.astype(np.int64)
+    keep = col[src] == col[dst]
+    s2, d2 = src[keep], dst[keep]
+    row_ptr = np.zeros(g.n + 1, dtype=np.uint64)
+    np.cumsum(np.bincount(s2, minlength=g.n), out=row_ptr[1:])
+    sub = _G(g.n, row_ptr, d2.astype(np.uint32))  # rows stay sorted: a filtered sorted row
+    c = count(orient(sub, "degree"), k)
+    return c, c * colors ** (k - 1)

@@ -1,12 +1,12 @@
 // Counting kernels: arb-count and arb-count-v (Algorithm 1, Section 3.2)
-// with the practical optimizations of Section 3.3, laid out for sm_103a.
+// with the practical optimizations of Section 3.4, laid out for sm_103a.
 //
 // Every k-clique is found exactly once, below its lowest vertex u in the total
 // order (the root), as a (k-1)-clique of the DAG induced on N+(u). For each
 // root the team (one warp when d+(u) <= 64, one block otherwise) builds that
-// induced subgraph once -- "the induced subgraph on N_DG(v)" of Section 3.3 --
+// induced subgraph once -- "the induced subgraph on N_DG(v)" of Section 3.4 --
 // as a bit matrix over positions 0..d-1 in N+(u) (the relabelling to
-// [0, O(alpha)] of Section 3.3). Out-lists are sorted by rank, so position
+// [0, O(alpha)] of Section 3.4). Out-lists are sorted by rank, so position
 // order is rank order: an arc between positions i < t points from i to t. One
 // matrix (adj) holds the subgraph: its upper triangle (bit t of row i, t > i)
 // is the arc set; per-vertex counting also fills the mirrored lower triangle,
@@ -21,7 +21,7 @@
 // set); a branch is cut when it has fewer candidates than vertices still
 // needed.
 //
-// Work split below the root (edge parallelism, Section 3.3): one warp item per
+// Work split below the root (edge parallelism, Section 3.4): one warp item per
 // arc u->x_i (k <= 5, and k >= 6 when the arc has at most 128 candidates) or
 // per triangle u->x_i->x_a (k >= 6 when the arc has more). For k >= 6 the
 // item's candidate set is compacted to local ids 0..s-1 (s <= 128, one or two

@@ -135,6 +135,9 @@ def _load():
                   lib.kc_server_release, lib.kc_server_get_stats):
             f.restype = I
         lib.kc_peel.argtypes = [ctypes.POINTER(_Csr), P, I, P, ctypes.POINTER(_PeelResult), P]
+        lib.kc_count_colorful.argtypes = [ctypes.POINTER(_Csr), I, U32, U64, I, ctypes.POINTER(U64),
+                                          ctypes.POINTER(ctypes.c_double), P]
+        lib.kc_count_colorful.restype = I
         lib.kc_peel.restype = I
         lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         lib.kc_measure_word_op_rate.restype = I
@@ -430,6 +433,20 @@ def kc_peel(row_ptr: torch.Tensor, col: torch.Tensor, dag: Dag, k: int, out: tor
     return ({f: int(getattr(res, f)) for f, _ in _PeelResult._fields_}, out[:n])
 
 
+def kc_count_colorful(row_ptr: torch.Tensor, col: torch.Tensor, k: int, colors: int, seed: int,
+                      method: str = "degree", stream=None):
+    """Colorful sparsification: (C, estimate) with C the exact k-clique count of
+    the monochromatic subgraph and estimate = C * colors^(k-1)."""
+    _require_cuda(row_ptr, "row_ptr", (torch.int64,))
+    _require_cuda(col, "col", (torch.int32,))
+    n = row_ptr.numel() - 1
+    g = _Csr(n, col.numel(), row_ptr.data_ptr(), col.data_ptr() if col.numel() else 0)
+    c, est = ctypes.c_uint64(), ctypes.c_double()
+    _check(_load().kc_count_colorful(ctypes.byref(g), int(k), int(colors), int(seed) & ((1 << 64) - 1),
+                                     _METHODS[method], ctypes.byref(c), ctypes.byref(est), _stream(stream)))
+    return int(c.value), float(est.value)
+
+
 def kc_dag_get_stats(dag: Dag, stream=None) -> dict:
     st = _Stats()
     _check(_load().kc_dag_get_stats(dag.handle, ctypes.byref(st), _stream(stream)))
@@ -456,6 +473,7 @@ count_per_vertex = kc_count_per_vertex
 count_per_arc = kc_count_per_arc
 count_batched = kc_count_batched
 peel = kc_peel
+count_colorful = kc_count_colorful
 autotune_batched = kc_autotune_batched
 dag_stats = kc_dag_get_stats
 
