@@ -47,10 +47,11 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_status_strings_without_gpu(lib_path):
     lib = ctypes.CDLL(lib_path)
     lib.kc_strerror.restype = ctypes.c_char_p
+    lib.kc_kernel_launches.restype = ctypes.c_uint64
+    before = lib.kc_kernel_launches()
     for code in range(7):
         assert lib.kc_strerror(code)
-    lib.kc_kernel_launches.restype = ctypes.c_uint64
-    assert lib.kc_kernel_launches() == 0
+    assert lib.kc_kernel_launches() == before  # no device work behind these calls
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
