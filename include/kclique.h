@@ -383,6 +383,18 @@ kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *d_round, kc
                   kc_stream_t stream);
 
 /*
+ * kc_peel_approx -- arb-approx-peel (Section 4.2): like kc_peel, but each
+ * round removes every remaining vertex whose count is at most
+ * floor(k (1 + eps) t / |S|) (t the k-cliques of the remaining set S,
+ * computed exactly in integers), which takes O(log n) rounds for eps > 0 and
+ * gives a 1/(k(1+eps))-approximation (Tsourakakis; Theorem of Section 4.2).
+ *   eps_num / eps_den  eps as a fraction (eps_den > 0)
+ * Other arguments and the result as for kc_peel.
+ */
+kc_status kc_peel_approx(const kc_csr *g, const kc_dag *d, int k, uint32_t eps_num, uint32_t eps_den,
+                         uint32_t *d_round, kc_peel_result *out, kc_stream_t stream);
+
+/*
  * Work statistics of an oriented graph, used for the bytes a counting pass
  * must move (computed exactly on the device):
  *   sum_out_sq     sum over roots u of d+(u)^2

@@ -19,6 +19,10 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   the appendix theorem (E[Y] = X, Var[Y] from the counts s_z of clique pairs
   sharing z vertices, computed by brute force); the color generator gives
   splitmix64's well-known first output for seed 0 (0xe220a8397b1dcdaf).
+* ``peel_approx`` (arb-approx-peel, Section 4.2): K_n in one round; the
+  1/(k(1+eps)) guarantee against a brute-force densest subset; at most
+  log_{1+eps}(n) + 1 rounds (each round removes at least an eps/(1+eps)
+  share of the remaining vertices, since the counts average k t / |S|).
 * ``peel`` (arb-peel, Algorithm 2): K_n in one round at C(n,k)/n; a disjoint
   K_a + K_b in two rounds at C(b,k)/b; no k-clique -> one round at 0; the
   1/k guarantee against a brute-force densest subset (n <= 12); peeling
@@ -313,6 +317,15 @@ class _G:
         return int(self.row_ptr[-1])
 
 
+def peel_approx(g, k: int, eps_num: int, eps_den: int):
+    """arb-approx-peel (Section 4.2) by its definition: every round removes the
+    remaining vertices whose k-clique count (in the graph induced by the
+    remaining set S) is at most floor(k (1 + eps) t(S) / |S|), eps =
+    eps_num / eps_den, in exact integers; counts recomputed from scratch
+    each round. Returns (PeelResult, rounds int64[n]) like peel."""
+    return _peel(g, k, (eps_num, eps_den))
+
+
 def peel(g, k: int):
     """arb-peel (Algorithm 2) by its definition: every round removes all
     remaining vertices whose k-clique count in the graph induced by the
@@ -321,6 +334,10 @@ def peel(g, k: int):
     counts incrementally). The best density (k-cliques per vertex) over the
     graph itself and every remainder is kept as an exact fraction.
     Returns (PeelResult, rounds int64[n])."""
+    return _peel(g, k, None)
+
+
+def _peel(g, k: int, eps):
     n = g.n
     rounds = np.full(n, -1, dtype=np.int64)
     keep = np.ones(n, dtype=bool)
@@ -333,8 +350,11 @@ def peel(g, k: int):
         if total is None:
             total = t
             best = (t, n, 0)
-        mn = pv.min()
-        peel_now = ids[pv == mn]
+        if eps is None:
+            peel_now = ids[pv == pv.min()]
+        else:
+            thr = (k * (eps[1] + eps[0]) * t) // (ids.size * eps[1])
+            peel_now = ids[pv <= thr]
         rounds[peel_now] = r
         keep[peel_now] = False
         remaining = int(keep.sum())

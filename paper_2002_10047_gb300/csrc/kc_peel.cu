@@ -1,5 +1,7 @@
 // arb-peel (Algorithm 2, Section 4.1): exact k-clique densest-subgraph
-// peeling, seeded by the per-vertex counts of arb-count-v.
+// peeling, seeded by the per-vertex counts of arb-count-v; and
+// arb-approx-peel (Section 4.2), which removes every vertex with at most
+// k(1+eps) times the current density in k-cliques each round.
 //
 // Every round peels all live vertices of minimum current k-clique count (the
 // set A). Update recounts only what A removes: for each v in A it counts the
@@ -53,13 +55,16 @@ __global__ void peel_min_kernel(const unsigned long long *__restrict__ C, const 
   if ((threadIdx.x & 31) == 0 && m != ~0ull) atomicMin(minv, m);
 }
 
-// A = live vertices with the minimum count; they get this round's index
+// A = live vertices whose count is at most the threshold (the minimum for
+// arb-peel, so exactly the vertices at the minimum; k(1+eps) times the
+// density for arb-approx-peel); they get this round's index. The threshold
+// is read from thr_ptr when it is given, else thr_value.
 __global__ void peel_mark_kernel(const unsigned long long *__restrict__ C, uint32_t *__restrict__ round, uint32_t n,
-                                 const unsigned long long *minv, uint32_t r, uint32_t *__restrict__ A,
-                                 unsigned *nA) {
-  const unsigned long long mv = *minv;
+                                 const unsigned long long *thr_ptr, unsigned long long thr_value, uint32_t r,
+                                 uint32_t *__restrict__ A, unsigned *nA) {
+  const unsigned long long mv = thr_ptr ? *thr_ptr : thr_value;
   for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
-    if (round[v] == kAlive && C[v] == mv) {
+    if (round[v] == kAlive && C[v] <= mv) {
       round[v] = r;
       A[atomicAdd(nA, 1u)] = (uint32_t)v;
     }
@@ -153,17 +158,20 @@ bool frac_gt(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
 }  // namespace
 }  // namespace kc
 
-extern "C" kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *d_round, kc_peel_result *out,
-                             kc_stream_t stream) {
+namespace {
+
+// Both peels; approx selects arb-approx-peel with epsilon = eps_num / eps_den.
+kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_t eps_num, uint64_t eps_den,
+                   uint32_t *d_round, kc_peel_result *out, cudaStream_t s) {
   using namespace kc;
   if (!g || !d || !out || k < 3 || k > KC_KMAX) return KC_EINVAL;
+  if (approx && eps_den == 0) return KC_EINVAL;
   if (g->n != d->n || g->nnz != 2 * d->m) return KC_EINVAL;
   const uint32_t n = d->n;
   memset(out, 0, sizeof *out);
   if (n == 0) return KC_OK;
   if (!d_round || !g->d_row_ptr || !d->key) return KC_EINVAL;
   if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
-  cudaStream_t s = (cudaStream_t)stream;
 
   DevBuf C, dec, A, len, rptr, rcol, scan_tmp, work, rorder;
   KC_CK(C.alloc(sizeof(unsigned long long) * n, s));
@@ -210,13 +218,24 @@ extern "C" kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *
   uint64_t best_num = total, best_den = n;
   uint32_t best_rounds = 0, r = 0;
   while (f < n) {
-    KC_CK(cudaMemsetAsync(d_min, 0xff, 8, s));
     KC_CK(cudaMemsetAsync(w + 8, 0, 8, s));
-    peel_min_kernel<<<grid_for(n, kPeelBlock), kPeelBlock, 0, s>>>(C.as<unsigned long long>(), d_round, n, d_min);
-    note_launch();
-    peel_mark_kernel<<<grid_for(n, kPeelBlock), kPeelBlock, 0, s>>>(C.as<unsigned long long>(), d_round, n, d_min, r,
-                                                                    A.as<uint32_t>(), d_nA);
-    note_launch();
+    if (approx) {
+      // threshold floor(k (1 + eps) t / |S|) with S the remaining vertices,
+      // exact in 128-bit integers: k (den + num) t / (|S| den)
+      const unsigned __int128 num = (unsigned __int128)(uint64_t)k * (eps_den + eps_num) * t_rem;
+      const unsigned __int128 q = num / ((unsigned __int128)(n - f) * eps_den);
+      const unsigned long long thr = q > (unsigned __int128)~0ull ? ~0ull : (unsigned long long)q;
+      peel_mark_kernel<<<grid_for(n, kPeelBlock), kPeelBlock, 0, s>>>(C.as<unsigned long long>(), d_round, n,
+                                                                      nullptr, thr, r, A.as<uint32_t>(), d_nA);
+      note_launch();
+    } else {
+      KC_CK(cudaMemsetAsync(d_min, 0xff, 8, s));
+      peel_min_kernel<<<grid_for(n, kPeelBlock), kPeelBlock, 0, s>>>(C.as<unsigned long long>(), d_round, n, d_min);
+      note_launch();
+      peel_mark_kernel<<<grid_for(n, kPeelBlock), kPeelBlock, 0, s>>>(C.as<unsigned long long>(), d_round, n, d_min,
+                                                                      0ull, r, A.as<uint32_t>(), d_nA);
+      note_launch();
+    }
     unsigned h_nA = 0;
     KC_CK(cudaMemcpyAsync(&h_nA, d_nA, 4, cudaMemcpyDeviceToHost, s));
     KC_CK(cudaStreamSynchronize(s));
@@ -310,4 +329,16 @@ extern "C" kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *
   out->best_vertices = best_den;
   out->total = total;
   return KC_OK;
+}
+
+}  // namespace
+
+extern "C" kc_status kc_peel(const kc_csr *g, const kc_dag *d, int k, uint32_t *d_round, kc_peel_result *out,
+                             kc_stream_t stream) {
+  return peel_run(g, d, k, false, 0, 1, d_round, out, (cudaStream_t)stream);
+}
+
+extern "C" kc_status kc_peel_approx(const kc_csr *g, const kc_dag *d, int k, uint32_t eps_num, uint32_t eps_den,
+                                    uint32_t *d_round, kc_peel_result *out, kc_stream_t stream) {
+  return peel_run(g, d, k, true, eps_num, eps_den, d_round, out, (cudaStream_t)stream);
 }

@@ -139,6 +139,8 @@ def _load():
                                           ctypes.POINTER(ctypes.c_double), P]
         lib.kc_count_colorful.restype = I
         lib.kc_peel.restype = I
+        lib.kc_peel_approx.argtypes = [ctypes.POINTER(_Csr), P, I, U32, U32, P, ctypes.POINTER(_PeelResult), P]
+        lib.kc_peel_approx.restype = I
         lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         lib.kc_measure_word_op_rate.restype = I
         lib.kc_kernel_launches.argtypes = []
@@ -416,8 +418,10 @@ class Server:
 
 
 def kc_peel(row_ptr: torch.Tensor, col: torch.Tensor, dag: Dag, k: int, out: torch.Tensor | None = None,
-            stream=None):
-    """arb-peel: (result dict, rounds int32[n]) for the CSR the DAG was oriented from.
+            stream=None, epsilon=None):
+    """arb-peel (epsilon None) or arb-approx-peel (epsilon >= 0, a float or a
+    Fraction, taken as a fraction with denominator <= 2^16): (result dict,
+    rounds int32[n]) for the CSR the DAG was oriented from.
 
     result: rounds, best_rounds, best_cliques, best_vertices (the best density
     is best_cliques / best_vertices, exactly), total."""
@@ -429,7 +433,16 @@ def kc_peel(row_ptr: torch.Tensor, col: torch.Tensor, dag: Dag, k: int, out: tor
     _require_cuda(out, "out", (torch.int32,))
     g = _Csr(n, col.numel(), row_ptr.data_ptr(), col.data_ptr() if col.numel() else 0)
     res = _PeelResult()
-    _check(_load().kc_peel(ctypes.byref(g), dag.handle, int(k), out.data_ptr(), ctypes.byref(res), _stream(stream)))
+    if epsilon is None:
+        _check(_load().kc_peel(ctypes.byref(g), dag.handle, int(k), out.data_ptr(), ctypes.byref(res),
+                               _stream(stream)))
+    else:
+        from fractions import Fraction
+        e = Fraction(epsilon).limit_denominator(1 << 16)
+        if e < 0:
+            raise ValueError("epsilon must be >= 0")
+        _check(_load().kc_peel_approx(ctypes.byref(g), dag.handle, int(k), e.numerator, e.denominator,
+                                      out.data_ptr(), ctypes.byref(res), _stream(stream)))
     return ({f: int(getattr(res, f)) for f, _ in _PeelResult._fields_}, out[:n])
 
 

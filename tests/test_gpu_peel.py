@@ -1,4 +1,5 @@
-"""GPU parity of arb-peel (Algorithm 2) through the C ABI: the round in which
+"""GPU parity of arb-peel (Algorithm 2) and arb-approx-peel (Section 4.2)
+through the C ABI: the round in which
 every vertex is removed, the number of rounds and the best density (an exact
 fraction) equal the oracle's peel, for both orientations (the result does
 not depend on the orientation)."""
@@ -97,3 +98,19 @@ def test_peel_larger_graph_invariants(kc):
         assert res["best_cliques"] * g.n >= res["total"] * res["best_vertices"]
     assert out["degree"][0] == out["gp"][0]
     assert np.array_equal(out["degree"][1], out["gp"][1])
+
+
+@pytest.mark.parametrize("name", ["er300", "ba500", "rmat9", "planted", "k40_plus_er"])
+def test_approx_peel_matches_oracle(kc, name):
+    from fractions import Fraction
+    make, ks = CASES[name]
+    g = make()
+    rp, col = kc.csr_to_device(g)
+    dag = kc.orient(rp, col, g.n)
+    for k in ks:
+        for eps in (Fraction(1, 10), Fraction(1, 2), Fraction(2, 1), Fraction(0)):
+            want, want_rounds = oracle.peel_approx(g, k, eps.numerator, eps.denominator)
+            res, rounds = kc.peel(rp, col, dag, k, epsilon=eps)
+            assert np.array_equal(rounds.cpu().numpy().astype(np.int64), want_rounds), (name, k, eps)
+            assert (res["rounds"], res["best_cliques"], res["best_vertices"], res["best_rounds"]) == \
+                (want.rounds, want.best_cliques, want.best_vertices, want.best_rounds), (name, k, eps)

@@ -1,10 +1,14 @@
-"""Pins of the oracle's arb-peel (Algorithm 2), on the CPU.
+"""Pins of the oracle's arb-peel (Algorithm 2) and arb-approx-peel (Section
+4.2), on the CPU.
 
 The peel is pinned by cases whose rounds and densities follow from closed
 forms (complete graphs, disjoint unions of two complete graphs, graphs
 without k-cliques), by a small graph worked by hand, by the 1/k guarantee
-(Section 4.1) against a brute-force densest subset, and by relabelling."""
+(Section 4.1) against a brute-force densest subset, and by relabelling; the
+approximate peel by complete graphs, its 1/(k(1+eps)) guarantee and its
+logarithmic round bound."""
 import itertools
+import math
 from fractions import Fraction
 from math import comb
 
@@ -85,3 +89,29 @@ def test_relabelling_moves_rounds_with_the_vertices():
     res2, rounds2 = oracle.peel(gg.relabel(g, perm), 3)
     assert res == res2
     assert np.array_equal(rounds2[perm.astype(np.int64)], rounds)
+
+
+@pytest.mark.parametrize("n,k", [(6, 3), (9, 4)])
+def test_approx_complete_graph_one_round(n, k):
+    res, rounds = oracle.peel_approx(gg.complete(n), k, 1, 2)
+    assert res.rounds == 1 and (rounds == 0).all()
+    assert (res.best_cliques, res.best_vertices) == (comb(n, k), n)
+
+
+@pytest.mark.parametrize("seed,k,eps", [(1, 3, (1, 2)), (3, 4, (1, 4)), (5, 3, (1, 1)), (2, 3, (0, 1))])
+def test_approx_guarantee(seed, k, eps):
+    g = gg.erdos_renyi(12, 0.55, seed)
+    res, _ = oracle.peel_approx(g, k, *eps)
+    dstar = Fraction(res.best_cliques, res.best_vertices)
+    opt = _densest_brute(g, k)
+    assert dstar <= opt
+    assert dstar >= opt / (k * (1 + Fraction(*eps)))
+
+
+@pytest.mark.parametrize("eps", [(1, 10), (1, 2), (2, 1)])
+def test_approx_round_bound(eps):
+    g = gg.rmat(10, 12, seed=3)
+    res, rounds = oracle.peel_approx(g, 4, *eps)
+    e = eps[0] / eps[1]
+    assert res.rounds <= math.ceil(math.log(g.n) / math.log1p(e)) + 1
+    assert rounds.min() == 0 and rounds.max() == res.rounds - 1
