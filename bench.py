@@ -1305,6 +1305,20 @@ def run_peel(args, rank, world):
             assert res2 == res
     t = sum(ms) / len(ms)
     t_max = max_over_ranks(t, world, dev)
+    # arb-approx-peel (Section 4.2) on the same graph, eps = 1/2
+    dag = kc.orient(rp, col, g.n, method="degree")
+    kc.peel(rp, col, dag, args.peel_k, out=rounds_buf, epsilon=0.5)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    res_a, _ = kc.peel(rp, col, dag, args.peel_k, out=rounds_buf, epsilon=0.5)
+    b.record(stream)
+    torch.cuda.synchronize()
+    dag.free()
+    approx = {"epsilon": 0.5, "ms": a.elapsed_time(b), "peel": res_a,
+              "best_density": res_a["best_cliques"] / max(1, res_a["best_vertices"]),
+              "density_ratio_to_exact": (res_a["best_cliques"] / max(1, res_a["best_vertices"]))
+              / max(1e-300, res["best_cliques"] / max(1, res["best_vertices"]))}
     if rank != 0:
         return
     line = {
@@ -1313,7 +1327,7 @@ def run_peel(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": peel_workload(args), "n": g.n, "m": g.m, "k": args.peel_k},
         "peel": res, "best_density": res["best_cliques"] / max(1, res["best_vertices"]),
-        "rounds_per_s": res["rounds"] / (t_max / 1e3), "clocks": clk.summary(),
+        "rounds_per_s": res["rounds"] / (t_max / 1e3), "approx_peel": approx, "clocks": clk.summary(),
         "note": "one host synchronisation per round (the next round's set depends on this round's counts)",
     }
     if not args.no_cpu_baseline:
