@@ -53,6 +53,9 @@ typedef enum {
 /* Orientation methods (Section 3.1; Section 5, "Algorithm Implementations"). */
 #define KC_ORIENT_DEGREE 0 /* rank by (degree, id), ascending */
 #define KC_ORIENT_GP 1     /* Goodrich-Pszona rounds, Algorithm 3 with epsilon = 1 */
+#define KC_ORIENT_BE 2     /* Barenboim-Elkin rounds (Section 3.1), epsilon = 1: remove every vertex of
+                              induced degree < 3 * alpha~, alpha~ = 4 * the approximate densest
+                              subgraph's density (removal rounds at degree <= 4 * density) */
 /* Flags or-ed into `method`: */
 #define KC_VALIDATE_SYMMETRY 0x100 /* also check that every arc u->v has v->u */
 
@@ -84,7 +87,7 @@ typedef struct kc_dag kc_dag;
  * higher endpoint ("direct the graph in CSR format ... using prefix sum and
  * filter", end of Section 3.1).
  *   g       the input CSR (device arrays)
- *   method  KC_ORIENT_DEGREE or KC_ORIENT_GP, optionally | KC_VALIDATE_SYMMETRY
+ *   method  KC_ORIENT_DEGREE, KC_ORIENT_GP or KC_ORIENT_BE, optionally | KC_VALIDATE_SYMMETRY
  *   out     receives a new handle on success (*out untouched on error)
  * The CSR is validated first (ascending rows, no self-loops, ids < n,
  * row_ptr consistent; symmetry on request): a violation gives KC_EINVAL.

@@ -19,6 +19,10 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   the appendix theorem (E[Y] = X, Var[Y] from the counts s_z of clique pairs
   sharing z vertices, computed by brute force); the color generator gives
   splitmix64's well-known first output for seed 0 (0xe220a8397b1dcdaf).
+* ``be_order`` (Barenboim-Elkin, Section 3.1): every out-degree is below
+  12 rho~ and rho~ <= rho* <= 4 rho~ against a brute-force densest subgraph;
+  a complete graph and a path worked by hand; counts equal those of every
+  other orientation.
 * ``peel_approx`` (arb-approx-peel, Section 4.2): K_n in one round; the
   1/(k(1+eps)) guarantee against a brute-force densest subset; at most
   log_{1+eps}(n) + 1 rounds (each round removes at least an eps/(1+eps)
@@ -125,7 +129,8 @@ def rank(g, method: str = "degree", perm=None) -> np.ndarray:
 
     methods: "degree" (non-decreasing degree, ties by id), "degeneracy"
     (Matula-Beck k-core order), "original" (ids), "gp" (Goodrich-Pszona,
-    Algorithm 3 with epsilon = 1), "perm" (the given ranks).
+    Algorithm 3 with epsilon = 1), "be" (Barenboim-Elkin, epsilon = 1, see
+    be_order), "perm" (the given ranks).
     """
     lib = _load()
     rp, col = _csr_arrays(g)
@@ -138,6 +143,8 @@ def rank(g, method: str = "degree", perm=None) -> np.ndarray:
         r[:g.n] = np.arange(g.n, dtype=np.uint32)
     elif method == "gp":
         _check(lib.or_rank_gp(g.n, _p(rp), _p(col), _p(r), None, None))
+    elif method == "be":
+        r[:g.n] = be_order(g)[0]
     elif method == "perm":
         r[:g.n] = np.asarray(perm, dtype=np.uint32)
     else:
@@ -404,3 +411,49 @@ def colorful_count(g, k: int, colors: int, seed: int):
     sub = _G(g.n, row_ptr, d2.astype(np.uint32))  # rows stay sorted: a filtered sorted row
     c = count(orient(sub, "degree"), k)
     return c, c * colors ** (k - 1)
+
+
+def _peel_rounds(g, deg, alive, thr_of):
+    """Rounds that remove every alive vertex whose induced degree is at most
+    thr_of(m_S, |S|), decrementing the induced degrees of the survivors.
+    Yields (selected mask, degrees at removal) per round."""
+    src = np.repeat(np.arange(g.n), np.diff(g.row_ptr.astype(np.int64)))
+    dst = g.col.astype(np.int64)
+    while alive.any():
+        S = int(alive.sum())
+        mS = int(deg[alive].sum()) // 2
+        sel = alive & (deg <= thr_of(mS, S))
+        if not sel.any():
+            raise OracleError("a removal round selected no vertex")
+        at_removal = deg.copy()
+        keep = alive & ~sel
+        e = sel[src] & keep[dst]
+        deg = deg - np.bincount(dst[e], minlength=g.n)
+        alive = keep
+        yield sel, at_removal, mS, S
+
+
+def be_order(g):
+    """Barenboim-Elkin order (Section 3.1) with epsilon = 1, as its steps read:
+    first the approximate densest subgraph -- rounds removing every vertex of
+    induced degree <= 2 (1 + eps) |E(S)| / |S| = 4 |E(S)| / |S|, keeping the
+    largest |E(S)| / |S| seen, rho~ -- then alpha~ = 2 (1 + eps) rho~ = 4 rho~
+    and rounds removing every vertex of induced degree < (2 + eps) alpha~ =
+    12 rho~ (integer division keeps both thresholds exact). Vertices are
+    ordered by (round, induced degree at removal, id).
+    Returns (rank, round, degree at removal, (rho~ numerator, denominator))."""
+    deg0 = np.diff(g.row_ptr.astype(np.int64))
+    best = (0, 1)
+    for _, _, mS, S in _peel_rounds(g, deg0.copy(), np.ones(g.n, dtype=bool), lambda m, s: (4 * m) // s):
+        if mS * best[1] > best[0] * S:
+            best = (mS, S)
+    thr = 0 if best[0] == 0 else (12 * best[0] - 1) // best[1]
+    rnd = np.zeros(g.n, dtype=np.int64)
+    dge = np.zeros(g.n, dtype=np.int64)
+    for r, (sel, at, _, _) in enumerate(_peel_rounds(g, deg0.copy(), np.ones(g.n, dtype=bool), lambda m, s: thr)):
+        rnd[sel] = r
+        dge[sel] = at[sel]
+    order = np.lexsort((np.arange(g.n), dge, rnd))
+    rank = np.empty(g.n, dtype=np.uint32)
+    rank[order] = np.arange(g.n, dtype=np.uint32)
+    return rank, rnd, dge, best

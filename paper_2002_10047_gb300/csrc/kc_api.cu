@@ -88,7 +88,7 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   if (!g || !out) return KC_EINVAL;
   const int base = method & 0xff;
   const int sym = (method & KC_VALIDATE_SYMMETRY) ? 1 : 0;
-  if (base != KC_ORIENT_DEGREE && base != KC_ORIENT_GP) return KC_EINVAL;
+  if (base != KC_ORIENT_DEGREE && base != KC_ORIENT_GP && base != KC_ORIENT_BE) return KC_EINVAL;
   if ((method & ~(0xff | KC_VALIDATE_SYMMETRY)) != 0) return KC_EINVAL;
   if (g->n > 0 && (!g->d_row_ptr || (g->nnz > 0 && !g->d_col))) return KC_EINVAL;
   if (g->nnz % 2 != 0) return KC_EINVAL;
@@ -135,7 +135,7 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   if (base == KC_ORIENT_DEGREE) {
     KC_CK(kc::launch_degree_key(*g, key.as<uint64_t>(), s));
   } else {
-    kc_status st = kc::gp_rank(*g, key.as<uint64_t>(), s);
+    kc_status st = base == KC_ORIENT_GP ? kc::gp_rank(*g, key.as<uint64_t>(), s) : kc::be_rank(*g, key.as<uint64_t>(), s);
     if (st != KC_OK) return st;
   }
   unsigned *d_max = status.as<unsigned>() + 1;

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "kc_internal.cuh"
 #include "kc_orient.cuh"
 
@@ -185,6 +187,125 @@ kc_status gp_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s) {
     if (b) cudaFreeAsync(b, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
   return KC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Barenboim-Elkin orientation (Section 3.1), epsilon = 1. Each round removes
+// every remaining vertex of induced degree below (2 + eps) * alpha~, where
+// alpha~ bounds the arboricity from the approximate densest subgraph: a
+// first peel removes, each round, the vertices of induced degree at most
+// 2 (1 + eps) rho(S), rho(S) = |E(S)| / |S|, and keeps the largest rho seen,
+// rho~; then rho* <= 2 (1 + eps) rho~ =: alpha~ for the densest subgraph's
+// density rho*, and every subgraph has a vertex of degree at most
+// 2 rho* < (2 + eps) alpha~, so each round removes at least one vertex (the
+// paper's argument gives a constant fraction). Thresholds are exact integer
+// fractions. The order key is (round << 32 | degree at removal), ties by id,
+// as for Goodrich-Pszona.
+
+__global__ void be_mark_kernel(const uint32_t *__restrict__ list, uint32_t cnt, const uint32_t *__restrict__ deg,
+                               uint32_t thr, uint32_t round, uint8_t *__restrict__ state,
+                               uint64_t *__restrict__ okey, uint32_t *__restrict__ sel, unsigned *sel_count,
+                               uint32_t cap) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cnt; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t v = list[i];
+    if (deg[v] <= thr) {
+      state[v] = 2;
+      if (okey) okey[v] = ((uint64_t)round << 32) | deg[v];
+      const unsigned at = atomicAdd(sel_count, 1u);
+      if (at < cap) sel[at] = v;
+    }
+  }
+}
+
+// sum of the induced degrees of the remaining vertices (2 |E(S)|)
+__global__ void be_degsum_kernel(const uint32_t *__restrict__ list, uint32_t cnt, const uint32_t *__restrict__ deg,
+                                 unsigned long long *sum) {
+  unsigned long long acc = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cnt; i += (size_t)gridDim.x * blockDim.x)
+    acc += deg[list[i]];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(sum, acc);
+}
+
+kc_status be_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s) {
+  const uint32_t n = g.n;
+  if (n == 0) return KC_OK;
+  uint32_t *deg = nullptr, *la = nullptr, *lb = nullptr, *sel = nullptr;
+  uint8_t *state = nullptr;
+  unsigned long long *cnts = nullptr;  // [0] degree sum, [1] selected, [2] kept
+  cudaError_t e = cudaSuccess;
+  auto ck = [&](cudaError_t x) {
+    if (e == cudaSuccess && x != cudaSuccess) e = x;
+  };
+  ck(cudaMallocAsync((void **)&deg, sizeof(uint32_t) * n, s));
+  ck(cudaMallocAsync((void **)&la, sizeof(uint32_t) * n, s));
+  ck(cudaMallocAsync((void **)&lb, sizeof(uint32_t) * n, s));
+  ck(cudaMallocAsync((void **)&sel, sizeof(uint32_t) * n, s));
+  ck(cudaMallocAsync((void **)&state, n, s));
+  ck(cudaMallocAsync((void **)&cnts, sizeof(unsigned long long) * 3, s));
+  kc_status st = KC_OK;
+  // phase 1: the approximate densest subgraph's density rho~ = best_m / best_n
+  // phase 2: Barenboim-Elkin rounds with threshold deg < 12 rho~ (eps = 1:
+  // (2 + eps) * 2 (1 + eps) = 12)
+  uint64_t best_m = 0, best_n = 1;
+  for (int phase = 0; phase < 2 && e == cudaSuccess && st == KC_OK; ++phase) {
+    gp_init_kernel<<<gp_grid(n), kBlock, 0, s>>>(g.d_row_ptr, n, deg, state, la);
+    note_launch();
+    uint32_t remaining = n, round = 0;
+    while (remaining > 0 && e == cudaSuccess) {
+      uint32_t thr;
+      if (phase == 0) {
+        ck(cudaMemsetAsync(cnts, 0, sizeof(unsigned long long), s));
+        be_degsum_kernel<<<gp_grid(remaining), kBlock, 0, s>>>(la, remaining, deg, cnts);
+        note_launch();
+        unsigned long long dsum = 0;
+        ck(cudaMemcpyAsync(&dsum, cnts, 8, cudaMemcpyDeviceToHost, s));
+        ck(cudaStreamSynchronize(s));
+        if (e != cudaSuccess) break;
+        const uint64_t mS = dsum / 2;
+        if ((unsigned __int128)mS * best_n > (unsigned __int128)best_m * remaining) {
+          best_m = mS;
+          best_n = remaining;
+        }
+        // deg <= 2 (1 + eps) mS / |S| = 4 mS / |S|
+        thr = (uint32_t)std::min<uint64_t>(0xffffffffu, (4 * mS) / remaining);
+      } else {
+        // deg < 12 best_m / best_n  <=>  deg <= floor((12 best_m - 1) / best_n)
+        thr = best_m == 0 ? 0u
+                          : (uint32_t)std::min<uint64_t>(0xffffffffu, (12 * best_m - 1) / best_n);
+      }
+      ck(cudaMemsetAsync(cnts + 1, 0, sizeof(unsigned long long) * 2, s));
+      be_mark_kernel<<<gp_grid(remaining), kBlock, 0, s>>>(la, remaining, deg, thr, round, state,
+                                                          phase == 1 ? okey : nullptr, sel,
+                                                          (unsigned *)(cnts + 1), n);
+      note_launch();
+      unsigned long long h_sel = 0;
+      ck(cudaMemcpyAsync(&h_sel, cnts + 1, 8, cudaMemcpyDeviceToHost, s));
+      ck(cudaStreamSynchronize(s));
+      if (e != cudaSuccess) break;
+      const uint32_t c = (uint32_t)(h_sel & 0xffffffffu);
+      if (c == 0 || c > remaining) {  // the bound above rules this out
+        st = KC_ECUDA;
+        break;
+      }
+      gp_decrement_kernel<<<gp_grid((size_t)c * 32), kBlock, 0, s>>>(sel, c, g.d_row_ptr, g.d_col, state, deg);
+      note_launch();
+      gp_compact_kernel<<<gp_grid(remaining), kBlock, 0, s>>>(la, remaining, state, lb, (unsigned *)(cnts + 2), n);
+      note_launch();
+      uint32_t *t = la;
+      la = lb;
+      lb = t;
+      remaining -= c;
+      ++round;
+      ck(cudaGetLastError());
+    }
+  }
+  void *bufs[] = {deg, la, lb, sel, state, cnts};
+  for (void *b : bufs)
+    if (b) cudaFreeAsync(b, s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
+  return st;
 }
 
 }  // namespace kc

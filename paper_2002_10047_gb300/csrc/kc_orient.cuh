@@ -26,6 +26,9 @@ cudaError_t launch_sort_rows(const uint64_t *ptr, uint32_t *col, const uint64_t 
                              cudaStream_t s);
 // Goodrich-Pszona order keys (kc_gp.cu): okey[v] = round << 32 | degree at removal
 kc_status gp_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s);
+// Barenboim-Elkin order keys (kc_gp.cu), epsilon = 1, arboricity bound from
+// the approximate densest subgraph: okey[v] = round << 32 | degree at removal
+kc_status be_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s);
 cudaError_t launch_dag_stats(const uint64_t *dp, const uint32_t *dc, uint32_t n, unsigned long long *acc,
                              cudaStream_t s);
 }  // namespace kc

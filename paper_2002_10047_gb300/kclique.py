@@ -24,10 +24,11 @@ KC_OK, KC_EINVAL, KC_ERANGE, KC_ENOMEM, KC_ETIMEDOUT, KC_ECUDA, KC_ECAPACITY = r
 KC_KMAX = 32
 KC_ORIENT_DEGREE = 0
 KC_ORIENT_GP = 1
+KC_ORIENT_BE = 2
 KC_VALIDATE_SYMMETRY = 0x100
 KC_LIGHT_BY_DEGREE = 1
 KC_LIGHT_BY_ID = 2
-_METHODS = {"degree": KC_ORIENT_DEGREE, "gp": KC_ORIENT_GP}
+_METHODS = {"degree": KC_ORIENT_DEGREE, "gp": KC_ORIENT_GP, "be": KC_ORIENT_BE}
 
 
 class KcError(RuntimeError):

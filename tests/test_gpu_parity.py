@@ -79,7 +79,7 @@ def graphs():
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
-@pytest.mark.parametrize("method", ["degree", "gp"])
+@pytest.mark.parametrize("method", ["degree", "gp", "be"])
 def test_orientation_bit_exact(kc, graphs, name, method):
     g = graphs[name]
     dag = gpu_orient(kc, g, method)

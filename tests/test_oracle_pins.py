@@ -39,7 +39,7 @@ def elem_sym(vals, k):
     return e[k]
 
 
-ORDERS = ["degree", "degeneracy", "original", "gp"]
+ORDERS = ["degree", "degeneracy", "original", "gp", "be"]
 
 
 def small_graphs():
