@@ -252,7 +252,10 @@ kc_status kc_count_batched(const kc_dag *d, const kc_batch *b, const kc_params *
  * synchronises `stream` and maps the device status of the last completed
  * launch to a kc_status (h_total, optional, receives the sum over graphs).
  * One plan's launches must not overlap on the GPU (they share its work
- * block); distinct plans are independent.
+ * block); distinct plans are independent. kc_plan_free releases the plan's
+ * buffers in the order of the stream it was created on: call it after the
+ * last launch has completed (kc_plan_result synchronises), or after that
+ * launch's stream has been made to wait on it.
  */
 typedef struct kc_plan kc_plan;
 kc_status kc_plan_create(const kc_dag *d, const kc_batch *b, const kc_params *prm, uint64_t *d_totals,
