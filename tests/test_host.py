@@ -42,3 +42,16 @@ def test_batch_recipe_ranges():
     assert min(s.avg_deg for s in specs) >= 4 and max(s.avg_deg for s in specs) <= 64
     assert {s.k for s in specs} == set(range(3, 9))
     assert gg.batch_specs(8, seed=3) == specs[:8]  # counter-based: a prefix is stable
+
+
+def test_device_csr_builder_equals_host_csr():
+    """The torch-sort CSR builder (input preparation for the 50M-vertex
+    workload) gives the same CSR as the host builder; run on the CPU here."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    eu, ev, _ = gg.chung_lu_planted_edges(n=200000, cliques=20)
+    g = gg.from_edges(200000, eu, ev)
+    rp, col = gg.csr_from_edges_on_device(200000, eu, ev, device="cpu")
+    assert np.array_equal(rp.numpy().view(np.uint64), g.row_ptr)
+    assert np.array_equal(col.numpy().view(np.uint32), g.col)
+    del torch
