@@ -376,7 +376,10 @@ kc_status kc_count_colorful(const kc_csr *g, int k, uint32_t colors, uint64_t se
  *            density as an exact fraction, reached by the vertices removed
  *            in rounds >= best_rounds (best_rounds = 0: the whole graph);
  *            total: k-cliques of the whole graph
- * Synchronises `stream` every round. KC_EINVAL if g and d differ in size.
+ * Synchronises `stream` every round. KC_EINVAL if g and d differ in size;
+ * KC_ECAPACITY if a vertex is removed while more than KC_MAX_OUT_DEGREE of
+ * its neighbours remain (its candidate row exceeds the counting kernels'
+ * root capacity).
  */
 typedef struct {
   uint32_t rounds;

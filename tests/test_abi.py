@@ -60,3 +60,20 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(kclique, "_lib", None)
     with pytest.raises(RuntimeError):
         kclique._load()
+
+
+def test_binding_checks_arguments_before_any_device_call(lib_path):
+    """The binding rejects host tensors and mismatched shapes itself (no
+    device is touched), for every entry point that takes tensors."""
+    torch = pytest.importorskip("torch")
+    from paper_2002_10047_gb300 import kclique as kc
+    rp = torch.zeros(5, dtype=torch.int64)
+    col = torch.zeros(0, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        kc.orient(rp, col, 4)
+    with pytest.raises(ValueError):
+        kc.Batch(torch.zeros(3, dtype=torch.int64), torch.zeros(2, dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        kc.count_colorful(rp, col, 3, 2, 1)
+    with pytest.raises(ValueError):
+        kc.peel(rp, col, None, 3)
