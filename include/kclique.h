@@ -421,6 +421,16 @@ typedef struct {
 kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t stream);
 
 /*
+ * kc_checked_sum -- the counting kernels' wrap-checked 64-bit reduction
+ * (thread sums, warp butterfly, one atomic per warp) applied to d_values
+ * (device uint64[n]): *h_total = their sum, or KC_ERANGE if the sum does not
+ * fit in uint64. (The paper has no counterpart: counts large enough to wrap
+ * cannot be enumerated in test time, so this exercises the overflow path.)
+ * Synchronises `stream`.
+ */
+kc_status kc_checked_sum(const uint64_t *d_values, uint64_t n, uint64_t *h_total, kc_stream_t stream);
+
+/*
  * Measured rate of the counting kernels' unit of integer work on the current
  * device: one 64-bit AND followed by a population count (the bitset form of
  * the intersect of Algorithm 1). Used as the roofline peak of the counting

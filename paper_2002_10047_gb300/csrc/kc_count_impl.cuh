@@ -39,6 +39,7 @@
 
 #include <mutex>
 
+#include "kc_checked.cuh"
 #include "kc_internal.cuh"
 
 namespace kc {
@@ -51,35 +52,12 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-__device__ __forceinline__ unsigned long long add_ck(unsigned long long a, unsigned long long b, unsigned &ovf) {
-  const unsigned long long s = a + b;
-  ovf |= (s < a) ? ST_OVERFLOW : 0u;
-  return s;
-}
-
-__device__ __forceinline__ void atomic_add_ck(unsigned long long *p, unsigned long long v, unsigned &ovf) {
-  if (v == 0) return;
-  const unsigned long long old = atomicAdd(p, v);
-  ovf |= (old + v < old) ? ST_OVERFLOW : 0u;
-}
-
 // Adds into a root's (or an item's) local per-vertex counters. No wrap check
 // is needed: an entry counts cliques of that root containing the vertex, so
 // it never exceeds the root's total, whose additions are checked; the flush
 // into the global per-vertex array is checked again.
 __device__ __forceinline__ void cnt_add(unsigned long long *p, unsigned long long v) {
   if (v) atomicAdd(p, v);
-}
-
-__device__ __forceinline__ unsigned long long warp_sum64_ck(unsigned long long v, unsigned &ovf) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long y = __shfl_xor_sync(0xffffffffu, v, o);
-    const unsigned long long s = v + y;
-    ovf |= (s < v) ? ST_OVERFLOW : 0u;
-    v = s;
-  }
-  return v;
 }
 
 __device__ __forceinline__ unsigned warp_incl_scan(unsigned v) {

@@ -142,6 +142,8 @@ def _load():
         lib.kc_peel.restype = I
         lib.kc_peel_approx.argtypes = [ctypes.POINTER(_Csr), P, I, U32, U32, P, ctypes.POINTER(_PeelResult), P]
         lib.kc_peel_approx.restype = I
+        lib.kc_checked_sum.argtypes = [P, U64, ctypes.POINTER(U64), P]
+        lib.kc_checked_sum.restype = I
         lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         lib.kc_measure_word_op_rate.restype = I
         lib.kc_kernel_launches.argtypes = []
@@ -466,6 +468,16 @@ def kc_dag_get_stats(dag: Dag, stream=None) -> dict:
     _check(_load().kc_dag_get_stats(dag.handle, ctypes.byref(st), _stream(stream)))
     return {"sum_out_sq": int(st.sum_out_sq), "sum_arc_head": int(st.sum_arc_head),
             "triangles": int(st.triangles), "max_out": int(st.max_out)}
+
+
+def kc_checked_sum(values: torch.Tensor, stream=None) -> int:
+    """Sum of a device int64 tensor read as uint64, through the counting
+    kernels' wrap-checked reduction (raises KcOverflow if it does not fit)."""
+    _require_cuda(values, "values", (torch.int64,))
+    t = ctypes.c_uint64()
+    _check(_load().kc_checked_sum(values.data_ptr() if values.numel() else None, values.numel(), ctypes.byref(t),
+                                  _stream(stream)))
+    return int(t.value)
 
 
 def kc_measure_word_op_rate(stream=None) -> float:
