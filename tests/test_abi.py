@@ -77,3 +77,19 @@ def test_binding_checks_arguments_before_any_device_call(lib_path):
         kc.count_colorful(rp, col, 3, 2, 1)
     with pytest.raises(ValueError):
         kc.peel(rp, col, None, 3)
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's constants are the header's (status codes, k range,
+    orientation methods and flags, warp-root orders)."""
+    from paper_2002_10047_gb300 import kclique as kc
+    text = open(os.path.join(ROOT, "include", "kclique.h")).read()
+    defines = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define (KC_\w+) (0x[0-9a-fA-F]+|\d+)\b", text)}
+    for name in ("KC_KMAX", "KC_ORIENT_DEGREE", "KC_ORIENT_GP", "KC_ORIENT_BE", "KC_VALIDATE_SYMMETRY",
+                 "KC_LIGHT_BY_DEGREE", "KC_LIGHT_BY_ID"):
+        assert getattr(kc, name) == defines[name], name
+    enum = dict((m.group(1), int(m.group(2))) for m in re.finditer(r"(KC_E?\w+) = (\d+)", text))
+    for name in ("KC_OK", "KC_EINVAL", "KC_ERANGE", "KC_ENOMEM", "KC_ETIMEDOUT", "KC_ECUDA", "KC_ECAPACITY"):
+        assert getattr(kc, name) == enum[name], name
+    assert kc._METHODS == {"degree": defines["KC_ORIENT_DEGREE"], "gp": defines["KC_ORIENT_GP"],
+                           "be": defines["KC_ORIENT_BE"]}
