@@ -150,14 +150,14 @@ kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_
  * any device memory. (The paper has no counterpart: this is an interface for
  * callers that cannot allocate.)
  *
- * Some callers cannot call cudaMalloc where they count: code running while a
- * stream is captured into a CUDA graph, code under a fixed memory budget or a
- * custom allocator that owns the device memory, or latency-critical paths that
- * must not take allocator locks. kc_count allocates a small work block (and,
- * for very large out-neighbourhoods, per-block matrices) on every call; this
- * entry point takes that scratch from one static device array of
- * KC_NOALLOC_SCRATCH_BYTES instead, which every GPU that loads the library
- * holds until the process exits.
+ * Some callers cannot call cudaMalloc where they count: code under a fixed
+ * memory budget or behind a custom allocator that owns the device memory (an
+ * allocation by this library would fail or escape the owner's accounting), or
+ * latency-critical paths that must not take allocator locks. kc_count
+ * allocates a small work block (and, for very large out-neighbourhoods,
+ * per-block matrices) on every call; this entry point takes that scratch from
+ * one static device array of KC_NOALLOC_SCRATCH_BYTES instead, which every
+ * GPU that loads the library holds until the process exits.
  *   d        a handle from kc_orient (created earlier, e.g. at set-up)
  *   k        1 .. KC_KMAX
  *   h_total  receives the count
@@ -168,7 +168,8 @@ kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_
  * overlap on the GPU, from different streams or threads, race and must be
  * serialised by the caller. Returns KC_ECAPACITY when one root's bit matrix
  * (largest out-degree about 8100 and up) does not fit the array; the other
- * status codes are those of kc_count.
+ * status codes are those of kc_count (a CUDA error is recorded for
+ * kc_last_cuda_error).
  */
 #define KC_NOALLOC_SCRATCH_BYTES (8u << 20)
 kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total, kc_stream_t stream);
@@ -422,7 +423,9 @@ kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t s
 
 /*
  * kc_checked_sum -- the counting kernels' wrap-checked 64-bit reduction
- * (thread sums, warp butterfly, one atomic per warp) applied to d_values
+ * (thread sums, then the block epilogue every counting kernel ends with: warp
+ * butterfly, the warps' sums added in the block, one atomic per block)
+ * applied to d_values
  * (device uint64[n]): *h_total = their sum, or KC_ERANGE if the sum does not
  * fit in uint64. (The paper has no counterpart: counts large enough to wrap
  * cannot be enumerated in test time, so this exercises the overflow path.)

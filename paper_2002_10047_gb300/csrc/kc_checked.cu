@@ -1,6 +1,8 @@
-// kc_checked_sum: the counting kernels' wrap-checked 64-bit reduction
-// (thread sums, warp butterfly, one atomic per warp), applied to a caller's
-// array. Counts large enough to wrap uint64 cannot be enumerated in test
+// kc_checked_sum: the counting kernels' wrap-checked 64-bit reduction applied
+// to a caller's array. Each thread sums its values with add_ck, and the block
+// then ends exactly as every counting kernel does, in finish_block (warp
+// butterfly, the warps' sums added by one thread, one checked atomic per
+// block). Counts large enough to wrap uint64 cannot be enumerated in test
 // time, so this is how the overflow path of the reductions is exercised.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -8,6 +10,7 @@
 #include <algorithm>
 
 #include "kc_checked.cuh"
+#include "kc_count_impl.cuh"
 #include "kc_host.cuh"
 
 namespace kc {
@@ -15,14 +18,15 @@ namespace {
 
 __global__ void checked_sum_kernel(const unsigned long long *__restrict__ v, uint64_t n, unsigned long long *total,
                                    unsigned *status) {
+  __shared__ unsigned long long red[kBlock / 32];
   unsigned ovf = 0;
   unsigned long long acc = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     acc = add_ck(acc, v[i], ovf);
-  acc = warp_sum64_ck(acc, ovf);
-  if ((threadIdx.x & 31) == 0) atomic_add_ck(total, acc, ovf);
-  ovf = __reduce_or_sync(0xffffffffu, ovf);
-  if ((threadIdx.x & 31) == 0 && ovf) atomicOr(status, ovf);
+  CountArgs a;
+  a.total = total;
+  a.status = status;
+  finish_block(a, acc, ovf, red, kBlock / 32);
 }
 
 }  // namespace
@@ -36,8 +40,8 @@ extern "C" kc_status kc_checked_sum(const uint64_t *d_values, uint64_t n, uint64
   KC_CK(work.alloc(16, s));
   KC_CK(cudaMemsetAsync(work.p, 0, 16, s));
   if (n > 0) {
-    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)sm_count() * 8));
-    checked_sum_kernel<<<grid, 256, 0, s>>>((const unsigned long long *)d_values, n, work.as<unsigned long long>(),
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((n + kBlock - 1) / kBlock, (uint64_t)sm_count() * 8));
+    checked_sum_kernel<<<grid, kBlock, 0, s>>>((const unsigned long long *)d_values, n, work.as<unsigned long long>(),
                                             (unsigned *)(work.as<uint8_t>() + 8));
     note_launch();
     KC_CK(cudaGetLastError());

@@ -1,10 +1,10 @@
 // kc_count_noalloc: the total k-clique count without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they count:
-// code that runs while a stream is being captured into a CUDA graph (where
-// cudaMalloc is not allowed), callers that run under a fixed memory budget
-// or a custom allocator that owns all of the device memory, and real-time
-// paths that must not take the allocator's locks. kc_count allocates a small
+// callers that run under a fixed memory budget or behind a custom allocator
+// that owns all of the device memory (a cudaMalloc from this library would
+// fail or break the owner's accounting), and latency-critical paths that must
+// not take the allocator's locks. kc_count allocates a small
 // work block (and, for very large out-neighbourhoods, per-block slabs) on every
 // call. This entry point takes that scratch from one statically sized device
 // array instead.
@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "kc_dag.cuh"
+#include "kc_host.cuh"
 #include "kc_internal.cuh"
 #include "kclique.h"
 
@@ -36,7 +37,7 @@ std::mutex g_mu;
 void *g_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device (looked up on the
-// first call for that device; it must not happen during stream capture).
+// first call for that device; make that first call before any stream capture).
 cudaError_t scratch_address(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -53,14 +54,8 @@ cudaError_t scratch_address(void **out) {
   return cudaSuccess;
 }
 
-int sm_count_here() {
-  int dev = 0, n = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  return n > 0 ? n : 1;
-}
-
 }  // namespace
+
 
 extern "C" kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total, kc_stream_t stream) {
   if (!d || !h_total || k < 1 || k > KC_KMAX) return KC_EINVAL;
@@ -82,18 +77,22 @@ extern "C" kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total,
 
   void *base = nullptr;
   cudaError_t e = scratch_address(&base);
-  if (e != cudaSuccess) return KC_ECUDA;
+  if (e != cudaSuccess) return kc::cuda_fail(e);
 
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int dev = 0, optin = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return kc::cuda_fail(e);
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return kc::cuda_fail(e);
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return kc::cuda_fail(e);
+  sms = std::max(1, sms);
   const size_t budget = (size_t)(optin > 4096 ? optin - 2048 : 48 * 1024);
   const uint32_t dcap = kc::block_root_capacity(budget, false, false);
   const uint32_t dsmem = std::min<uint32_t>(dcap, std::max<uint32_t>(d->max_out, kc::kLightMax + 1));
   const size_t block_smem = kc::block_root_smem(dsmem, false, false);
   int per_sm_b = 0, per_sm_w = 0;
-  if (kc::count_occupancy(false, false, block_smem, &per_sm_b, &per_sm_w) != cudaSuccess) return KC_ECUDA;
-  const int sms = sm_count_here();
+  if ((e = kc::count_occupancy(false, false, block_smem, &per_sm_b, &per_sm_w)) != cudaSuccess)
+    return kc::cuda_fail(e);
   const int block_grid = sms * std::max(1, per_sm_b);
   const int warp_grid = sms * std::max(1, per_sm_w);
 
@@ -123,11 +122,12 @@ extern "C" kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total,
     a.scratch_blocks = (uint32_t)nb;
   }
   // the work block keeps the previous call's values: clear it first
-  if (cudaMemsetAsync(b, 0, 64, s) != cudaSuccess) return KC_ECUDA;
-  if (kc::launch_count(a, false, false, block_grid, warp_grid, block_smem, s) != cudaSuccess) return KC_ECUDA;
+  if ((e = cudaMemsetAsync(b, 0, 64, s)) != cudaSuccess) return kc::cuda_fail(e);
+  if ((e = kc::launch_count(a, false, false, block_grid, warp_grid, block_smem, s)) != cudaSuccess)
+    return kc::cuda_fail(e);
   unsigned long long h[2] = {0, 0};
-  if (cudaMemcpyAsync(h, b, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess) return KC_ECUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return KC_ECUDA;
+  if ((e = cudaMemcpyAsync(h, b, sizeof h, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return kc::cuda_fail(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return kc::cuda_fail(e);
   const unsigned st = (unsigned)h[1];
   if (st & kc::ST_CAPACITY) return KC_ECAPACITY;
   if (st & kc::ST_OVERFLOW) return KC_ERANGE;

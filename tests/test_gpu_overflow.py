@@ -1,7 +1,8 @@
 """The overflow path of the count reductions: the counting kernels' checked
-64-bit reduction, driven through kc_checked_sum with sums that fit exactly
-and sums one past 2^64 - 1 (in a thread, inside a warp, and across warps),
-which must raise instead of wrapping."""
+64-bit reduction (thread sums and the block epilogue the counting kernels end
+with), driven through kc_checked_sum with sums that fit exactly and sums one
+past 2^64 - 1 (in a thread, inside a warp, between the warps of one block,
+and across blocks), which must raise instead of wrapping."""
 import numpy as np
 import pytest
 
@@ -39,6 +40,7 @@ def test_sums_that_fit_are_exact(kc):
     [1 << 63, 1 << 63],                                  # two lanes of one warp
     [(1 << 64) - 1, 1],
     [(1 << 62)] * 4,                                     # exactly 2^64
+    [1 << 63] + [0] * 31 + [1 << 63],                    # lane 0 of warps 0 and 1 of block 0
 ])
 def test_small_overflows_raise(kc, vals):
     with pytest.raises(kc.KcOverflow):
@@ -46,7 +48,7 @@ def test_small_overflows_raise(kc, vals):
 
 
 def test_overflow_across_warps_and_blocks_raises(kc):
-    # 2^21 values of 2^43 sum to exactly 2^64: no single thread or warp wraps,
-    # the wrap happens in the cross-warp atomic accumulation
+    # 2^21 values of 2^43 sum to exactly 2^64: no single thread, warp or block
+    # wraps, the wrap happens in the per-block atomic accumulation
     with pytest.raises(kc.KcOverflow):
         kc.kc_checked_sum(dev(np.full(1 << 21, 1 << 43, dtype=np.uint64)))
