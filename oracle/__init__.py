@@ -33,7 +33,13 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   rounds follow a relabelling of the vertices.
 * ``orient`` (degree / degeneracy / original / gp): every ordering yields an
   acyclic orientation that keeps each edge once; the degree and GP orders
-  are checked against their defining properties on hand-made graphs.
+  are checked against their defining properties on hand-made graphs. The
+  degeneracy (smallest-last) order is recomputed step by step from a dense
+  matrix (each removed vertex has the minimum remaining degree, smallest id
+  first), and its largest out-degree equals the degeneracy: 1 for trees, 2
+  for cycles and grids, n - 1 for K_n, n minus the largest part for Turan
+  graphs, and the brute-force maximum over all vertex subsets of the
+  minimum degree on random graphs.
 """
 from __future__ import annotations
 

@@ -61,42 +61,66 @@ int or_rank_degree(uint32_t n, const uint64_t *row_ptr, uint32_t *rank) {
   return OR_OK;
 }
 
-/* k-core (degeneracy) ordering of Matula and Beck: repeatedly remove a vertex
- * of minimum remaining degree; rank = removal position. Bucket queue in the
- * array form of Batagelj and Zaversnik. */
+/* Binary min-heap of 64-bit keys (the degeneracy order's priority queue). */
+static void heap_push(uint64_t *h, size_t *len, uint64_t x) {
+  size_t i = (*len)++;
+  while (i > 0) {
+    size_t p = (i - 1) / 2;
+    if (h[p] <= x) break;
+    h[i] = h[p];
+    i = p;
+  }
+  h[i] = x;
+}
+
+static uint64_t heap_pop(uint64_t *h, size_t *len) {
+  uint64_t top = h[0], x = h[--(*len)];
+  size_t i = 0;
+  for (;;) {
+    size_t c = 2 * i + 1;
+    if (c >= *len) break;
+    if (c + 1 < *len && h[c + 1] < h[c]) c++;
+    if (x <= h[c]) break;
+    h[i] = h[c];
+    i = c;
+  }
+  if (*len) h[i] = x;
+  return top;
+}
+
+/* k-core (degeneracy) ordering, smallest-last as Matula and Beck define it:
+ * repeatedly remove the vertex of minimum degree in the graph induced by the
+ * vertices not yet removed, ties broken by the smaller id; rank = removal
+ * position. The queue holds (degree << 32 | id) keys; a vertex whose degree
+ * drops is pushed again with its new key, and popped keys that no longer
+ * match a live vertex's degree are skipped. */
 int or_rank_degeneracy(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, uint32_t *rank) {
   if (n == 0) return OR_OK;
-  uint32_t maxd = 0;
+  size_t cap = (size_t)n + (size_t)row_ptr[n] + 1, len = 0;
   uint32_t *deg = (uint32_t *)malloc(sizeof(uint32_t) * n);
-  uint32_t *vert = (uint32_t *)malloc(sizeof(uint32_t) * n);
-  uint32_t *pos = (uint32_t *)malloc(sizeof(uint32_t) * n);
-  if (!deg || !vert || !pos) { free(deg); free(vert); free(pos); return OR_ENOMEM; }
+  uint8_t *gone = (uint8_t *)calloc(n, 1);
+  uint64_t *heap = (uint64_t *)malloc(sizeof(uint64_t) * cap);
+  if (!deg || !gone || !heap) { free(deg); free(gone); free(heap); return OR_ENOMEM; }
   for (uint32_t v = 0; v < n; v++) {
     deg[v] = (uint32_t)(row_ptr[v + 1] - row_ptr[v]);
-    if (deg[v] > maxd) maxd = deg[v];
+    heap_push(heap, &len, ((uint64_t)deg[v] << 32) | v);
   }
-  uint32_t *bin = (uint32_t *)calloc((size_t)maxd + 2, sizeof(uint32_t));
-  if (!bin) { free(deg); free(vert); free(pos); return OR_ENOMEM; }
-  for (uint32_t v = 0; v < n; v++) bin[deg[v]]++;
-  uint32_t start = 0;
-  for (uint32_t d = 0; d <= maxd; d++) { uint32_t num = bin[d]; bin[d] = start; start += num; }
-  for (uint32_t v = 0; v < n; v++) { pos[v] = bin[deg[v]]; vert[pos[v]] = v; bin[deg[v]]++; }
-  for (uint32_t d = maxd; d >= 1; d--) bin[d] = bin[d - 1];
-  bin[0] = 0;
-  for (uint32_t i = 0; i < n; i++) {
-    uint32_t v = vert[i];
-    rank[v] = i;
+  uint32_t removed = 0;
+  while (removed < n) {
+    uint64_t key = heap_pop(heap, &len);
+    uint32_t v = (uint32_t)key;
+    if (gone[v] || (uint32_t)(key >> 32) != deg[v]) continue;  /* stale entry */
+    gone[v] = 1;
+    rank[v] = removed++;
     for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; e++) {
       uint32_t u = col[e];
-      if (deg[u] > deg[v]) {
-        uint32_t du = deg[u], pu = pos[u], pw = bin[du], w = vert[pw];
-        if (u != w) { pos[u] = pw; vert[pu] = w; pos[w] = pu; vert[pw] = u; }
-        bin[du]++;
+      if (!gone[u]) {
         deg[u]--;
+        heap_push(heap, &len, ((uint64_t)deg[u] << 32) | u);
       }
     }
   }
-  free(deg); free(vert); free(pos); free(bin);
+  free(deg); free(gone); free(heap);
   return OR_OK;
 }
 

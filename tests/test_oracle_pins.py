@@ -242,6 +242,87 @@ def test_orientations_are_acyclic_and_complete():
             assert np.all(key[src] < key[dag.adj.astype(np.int64)])
 
 
+def _degeneracy_brute(g):
+    """max over all vertex subsets S of the minimum degree in G[S] (the
+    definition of degeneracy); for n <= ~16."""
+    A = gg.dense_adjacency(g).astype(np.int64)
+    best = 0
+    for mask in range(1, 1 << g.n):
+        idx = [i for i in range(g.n) if mask >> i & 1]
+        best = max(best, int(A[np.ix_(idx, idx)].sum(1).min()))
+    return best
+
+
+def _max_out(dag):
+    return int(np.diff(dag.ptr.astype(np.int64)).max()) if dag.n else 0
+
+
+def _degeneracy_graphs():
+    rng = np.random.default_rng(33)
+    out = [("rmat9", gg.rmat(9, 10, seed=91)), ("ba300", gg.barabasi_albert(300, 4, 5)),
+           ("er400", gg.erdos_renyi(400, 0.03, 6)), ("turan", gg.turan([7, 5, 5, 2])),
+           ("planted", gg.disjoint_union([gg.complete(9), gg.erdos_renyi(60, 0.1, 8), gg.complete(4)]))]
+    n = 200  # R-MAT-like skew plus a planted clique on random ids
+    g = gg.rmat(8, 6, seed=12)
+    ids = rng.choice(g.n, 12, replace=False)
+    eu, ev = g.edges()
+    pu, pv = zip(*itertools.combinations(ids.tolist(), 2))
+    out.append(("rmat8_planted", gg.from_edges(g.n, np.r_[eu, pu], np.r_[ev, pv])))
+    return out
+
+
+@pytest.mark.parametrize("name,g", _degeneracy_graphs())
+def test_degeneracy_order_removes_a_minimum_degree_vertex(name, g):
+    """Smallest-last (Matula-Beck), the k-core order of Section 5: each vertex,
+    when its rank comes, has the minimum degree in the graph induced by the
+    vertices not yet removed, and is the smallest id among those of that
+    degree; recomputed here from a dense matrix, step by step. The largest
+    out-degree of the orientation is the largest such minimum degree."""
+    r = oracle.rank(g, "degeneracy").astype(np.int64)
+    order = np.argsort(r)
+    assert np.array_equal(r[order], np.arange(g.n))
+    A = gg.dense_adjacency(g).astype(np.int64)
+    deg = A.sum(1)
+    alive = np.ones(g.n, dtype=bool)
+    dmax = 0
+    for v in order:
+        cand = np.nonzero(alive)[0]
+        want = cand[np.lexsort((cand, deg[cand]))[0]]
+        assert v == want, (name, int(v), int(want))
+        dmax = max(dmax, int(deg[v]))
+        alive[v] = False
+        deg -= A[v]
+    assert _max_out(oracle.orient(g, "degeneracy")) == dmax
+
+
+def test_degeneracy_closed_forms():
+    """The largest out-degree of the degeneracy orientation equals the
+    degeneracy: 1 for a tree, 2 for a cycle and a grid, n - 1 for K_n, n minus
+    the largest part for a complete multipartite (Turan) graph, s - 1 for
+    disjoint cliques of size up to s, 0 with no edge; and the brute-force
+    maximum of the minimum degree over all vertex subsets on random graphs."""
+    rng = np.random.default_rng(5)
+    n = 300
+    parent = np.array([int(rng.integers(0, i)) for i in range(1, n)], dtype=np.uint32)
+    tree = gg.from_edges(n, np.arange(1, n, dtype=np.uint32), parent)
+    cyc = gg.from_edges(50, np.arange(50, dtype=np.uint32), (np.arange(50, dtype=np.uint32) + 1) % 50)
+    R, C = 9, 13
+    v = np.arange(R * C).reshape(R, C)
+    grid = gg.from_edges(R * C, np.r_[v[:, :-1].ravel(), v[:-1, :].ravel()],
+                         np.r_[v[:, 1:].ravel(), v[1:, :].ravel()])
+    cases = [(tree, 1), (cyc, 2), (grid, 2), (gg.complete(23), 22), (gg.empty(7), 0),
+             (gg.turan([6, 4, 4, 3]), 17 - 6), (gg.turan([9, 1]), 1),
+             (gg.disjoint_union([gg.complete(5), gg.complete(11), gg.complete(3)]), 10)]
+    for g, want in cases:
+        assert _max_out(oracle.orient(g, "degeneracy")) == want
+    for seed in range(6):
+        g = gg.erdos_renyi(13, 0.25 + 0.1 * seed, 40 + seed)
+        assert _max_out(oracle.orient(g, "degeneracy")) == _degeneracy_brute(g)
+    # the degree order can be worse than the degeneracy, never better
+    g = gg.rmat(9, 10, seed=91)
+    assert _max_out(oracle.orient(g, "degree")) >= _max_out(oracle.orient(g, "degeneracy"))
+
+
 def _read_golden(name):
     rows = []
     with open(os.path.join(GOLDEN, name)) as f:
