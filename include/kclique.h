@@ -146,6 +146,26 @@ kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_
                            kc_stream_t stream);
 
 /*
+ * kc_count_roots -- rooted counts of a list of roots: d_out[i] = number of
+ * k-cliques whose lowest vertex in the total order is d_roots[i], i.e. the
+ * term that the top call of Algorithm 1 adds for that vertex (every clique is
+ * found once, below its lowest vertex). Summed over all vertices this is
+ * kc_count; over a subset of roots it is that subset's share, which serves
+ * sampled checks on graphs too large to count whole and partitions of the
+ * roots between independent passes.
+ *   d_roots    device uint32[num_roots], distinct vertex ids < n; borrowed
+ *   num_roots  may be 0
+ *   d_out      device uint64[num_roots], caller-owned; overwritten
+ *   h_total    optional (NULL allowed): the sum of d_out
+ *   k          1 .. KC_KMAX (k = 1: 1 per root; k = 2: the root's out-degree)
+ * The roots are copied to the host and ordered there by out-degree, then
+ * counted by the same persistent kernels as kc_count. Synchronises `stream`.
+ * KC_EINVAL for an id >= n or a repeated id; KC_ERANGE on uint64 overflow.
+ */
+kc_status kc_count_roots(const kc_dag *d, int k, const uint32_t *d_roots, uint32_t num_roots, uint64_t *d_out,
+                         uint64_t *h_total, kc_stream_t stream);
+
+/*
  * kc_count_noalloc -- the same total as kc_count, computed without allocating
  * any device memory. (The paper has no counterpart: this is an interface for
  * callers that cannot allocate.)

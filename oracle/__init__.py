@@ -14,6 +14,9 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   cliques, and the 4-clique fragment of the paper's worked example
   (Appendix A, Figure 7; the figure itself is missing, so that pin is partial).
 * ``count_arc``: sums over all arcs equal ``count`` (k >= 2).
+* ``count_containing`` (k-cliques through one vertex, via its neighbourhood):
+  equal to brute force per vertex (n <= 16), to C(n-1, k-1) on K_n, and its
+  sum over the vertices is k times the total.
 * ``colorful_count`` (colorful sparsification, Section 3.3): one color gives
   the exact count; over many seeds the estimate's mean and variance match
   the appendix theorem (E[Y] = X, Var[Y] from the counts s_z of clique pairs
@@ -258,6 +261,39 @@ def count_arc(dag: Dag, k: int, u: int, v: int) -> int:
     if t >= 1 << 64:
         raise OracleOverflow("count does not fit in uint64")
     return int(t)
+
+
+def neighbourhood(g, v: int):
+    """The subgraph induced by N(v) (undirected neighbours of v), its vertex i
+    being the i-th neighbour of v in id order."""
+    rp = np.asarray(g.row_ptr, dtype=np.int64)
+    nb = np.asarray(g.col[rp[v]:rp[v + 1]], dtype=np.int64)
+    src, dst = [], []
+    for i, w in enumerate(nb):
+        row = np.asarray(g.col[rp[w]:rp[w + 1]], dtype=np.int64)
+        pos = np.searchsorted(nb, row)
+        hit = pos < nb.size
+        hit[hit] = nb[pos[hit]] == row[hit]
+        src.append(np.full(int(hit.sum()), i, dtype=np.int64))
+        dst.append(pos[hit])
+    s2 = np.concatenate(src) if src else np.zeros(0, np.int64)
+    d2 = np.concatenate(dst) if dst else np.zeros(0, np.int64)
+    order = np.lexsort((d2, s2))
+    row_ptr = np.zeros(nb.size + 1, dtype=np.uint64)
+    np.cumsum(np.bincount(s2, minlength=nb.size), out=row_ptr[1:])
+    return _G(int(nb.size), row_ptr, d2[order].astype(np.uint32))
+
+
+def count_containing(g, k: int, v: int) -> int:
+    """Number of k-cliques that contain v, from the definition: such a clique
+    is v together with a (k-1)-clique of the subgraph induced by N(v). This
+    is the per-vertex count of Section 3.2 computed without any per-vertex
+    bookkeeping."""
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    if k == 1:
+        return 1
+    return count(orient(neighbourhood(g, v), "degree"), k - 1)
 
 
 def brute(g, k: int) -> tuple[int, np.ndarray]:

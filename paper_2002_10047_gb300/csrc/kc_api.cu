@@ -239,6 +239,8 @@ cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_pa
   if (light < 2) light = 2;
   const uint32_t dsmem = std::min<uint32_t>(dcap, std::max<uint32_t>(d->max_out, light + 1));
   P.block_smem = block_root_smem(dsmem, pv, pa);
+  P.dcap = dcap;
+  P.light = light;
   int per_sm_b = 0, per_sm_w = 0;
   cudaError_t e = count_occupancy(pv, pa, P.block_smem, &per_sm_b, &per_sm_w);
   if (e != cudaSuccess) return e;
@@ -326,6 +328,103 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
   return KC_OK;
 }
 
+// Rooted counts of a list of roots: the roots are ordered by out-degree
+// (descending) on the host, split into the same three classes as a whole
+// pass, and counted by the same two kernels, each root writing its total to
+// its caller position.
+kc_status run_count_roots(const kc_dag *d, int k, const uint32_t *d_roots, uint32_t r, uint64_t *d_out,
+                          uint64_t *h_total, cudaStream_t s) {
+  if (!d || k < 1 || k > KC_KMAX || (r > 0 && (!d_roots || !d_out))) return KC_EINVAL;
+  if (r == 0) {
+    if (h_total) *h_total = 0;
+    return KC_OK;
+  }
+  std::vector<uint32_t> roots(r);
+  KC_CK(cudaMemcpyAsync(roots.data(), d_roots, sizeof(uint32_t) * r, cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  {
+    std::vector<uint32_t> sorted(roots);
+    std::sort(sorted.begin(), sorted.end());
+    if (sorted.back() >= d->n) return KC_EINVAL;
+    for (uint32_t i = 1; i < r; ++i)
+      if (sorted[i] == sorted[i - 1]) return KC_EINVAL;
+  }
+  DevBuf ddeg;
+  KC_CK(ddeg.alloc(sizeof(uint32_t) * r, s));
+  KC_CK(launch_root_outdeg(d->ptr, d_roots, r, ddeg.as<uint32_t>(), s));
+  std::vector<uint32_t> deg(r);
+  KC_CK(cudaMemcpyAsync(deg.data(), ddeg.p, sizeof(uint32_t) * r, cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  if (k <= 2) {  // one 1-clique per root; its out-arcs are the 2-cliques it roots
+    std::vector<uint64_t> out(r);
+    uint64_t t = 0;
+    for (uint32_t i = 0; i < r; ++i) t += (out[i] = k == 1 ? 1u : deg[i]);
+    KC_CK(cudaMemcpyAsync(d_out, out.data(), sizeof(uint64_t) * r, cudaMemcpyHostToDevice, s));
+    KC_CK(cudaStreamSynchronize(s));
+    if (h_total) *h_total = t;
+    return KC_OK;
+  }
+  KC_CK(cudaMemsetAsync(d_out, 0, sizeof(uint64_t) * r, s));
+  const uint32_t need = (uint32_t)(k - 1);
+  if (need > d->max_out) {
+    KC_CK(cudaStreamSynchronize(s));
+    if (h_total) *h_total = 0;
+    return KC_OK;
+  }
+  if (d->max_out > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
+  LaunchPlan P;
+  KC_CK(plan_count(d, k, false, false, nullptr, &P));
+  CountArgs &a = P.a;
+  std::vector<uint32_t> idx(r);
+  for (uint32_t i = 0; i < r; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](uint32_t x, uint32_t y) { return deg[x] > deg[y]; });
+  std::vector<uint32_t> hb(2 * (size_t)r);  // order, then caller positions
+  uint32_t n_scratch = 0, n_big = 0, n_end = 0, dmax = 0;
+  for (uint32_t i = 0; i < r; ++i) {
+    const uint32_t dg = deg[idx[i]];
+    hb[i] = roots[idx[i]];
+    hb[r + i] = idx[i];
+    n_scratch += dg > P.dcap;
+    n_big += dg > P.light;
+    n_end += dg >= need;
+    dmax = std::max(dmax, dg);
+  }
+  DevBuf ord, work, scratch;
+  KC_CK(ord.alloc(sizeof(uint32_t) * 2 * (size_t)r, s));
+  KC_CK(cudaMemcpyAsync(ord.p, hb.data(), sizeof(uint32_t) * 2 * (size_t)r, cudaMemcpyHostToDevice, s));
+  a.order = ord.as<uint32_t>();
+  a.rooted_pos = ord.as<uint32_t>() + r;
+  a.rooted = (unsigned long long *)d_out;
+  a.n_scratch = n_scratch;
+  a.n_big = std::max(n_big, n_scratch);
+  a.n_light_end = std::max(n_end, a.n_big);
+  a.light_by_id = 0;
+  a.scratch_blocks = 0;
+  P.scratch_bytes = 0;
+  if (n_scratch > 0) {
+    const size_t slab = (root_layout(dmax, false, false).bytes + 255) & ~(size_t)255;
+    size_t nb = std::max<size_t>(1, ((size_t)4 << 30) / slab);
+    nb = std::min<size_t>(nb, (size_t)P.block_grid);
+    nb = std::min<size_t>(nb, (size_t)n_scratch);
+    a.scratch_stride = slab;
+    a.scratch_blocks = (uint32_t)nb;
+    P.scratch_bytes = slab * nb;
+    KC_CK(scratch.alloc(P.scratch_bytes, s));
+    a.scratch = scratch.as<uint8_t>();
+  }
+  KC_CK(work.alloc(kc_work_bytes(), s));
+  KC_CK(cudaMemsetAsync(work.p, 0, kc_work_bytes(), s));
+  set_work(&a, work.as<uint8_t>());
+  KC_CK(launch_count(a, false, false, P.block_grid, P.warp_grid, P.block_smem, s));
+  unsigned long long h[2] = {0, 0};
+  KC_CK(cudaMemcpyAsync(h, work.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  const kc_status code = status_code((unsigned)h[1]);
+  if (code != KC_OK) return code;
+  if (h_total) *h_total = h[0];
+  return KC_OK;
+}
+
 }  // namespace kc
 
 extern "C" {
@@ -343,6 +442,11 @@ kc_status kc_count_per_vertex(const kc_dag *d, int k, uint64_t *d_out, uint64_t 
 kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_total, kc_stream_t stream) {
   if (!d_out) return KC_EINVAL;
   return kc::run_count(d, k, nullptr, (unsigned long long *)d_out, h_total, 0, (cudaStream_t)stream);
+}
+
+kc_status kc_count_roots(const kc_dag *d, int k, const uint32_t *d_roots, uint32_t num_roots, uint64_t *d_out,
+                         uint64_t *h_total, kc_stream_t stream) {
+  return kc::run_count_roots(d, k, d_roots, num_roots, d_out, h_total, (cudaStream_t)stream);
 }
 
 }  // extern "C"

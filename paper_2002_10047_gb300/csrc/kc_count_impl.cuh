@@ -716,8 +716,8 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned long lo
 }
 
 template <bool PV, bool PA>
-__device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8_t *base, uint8_t *slots, unsigned long long &tsum_out,
-                           unsigned &ovf_out, BlockShared &sh) {
+__device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint32_t oi, uint8_t *base, uint8_t *slots,
+                                           unsigned long long &tsum_out, unsigned &ovf_out, BlockShared &sh) {
   unsigned ovf = 0;
   unsigned long long tsum = 0;
   const unsigned tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
@@ -929,7 +929,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
     }
   }
   __syncthreads();
-  if (PV || a.gtotal) {
+  if (PV || a.gtotal || a.rooted) {
     const unsigned long long r = warp_sum64_ck(rsum, ovf);
     if (lane == 0) sh.red[warp] = r;
     __syncthreads();
@@ -938,6 +938,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint8
       for (int w = 0; w < kRootWarps; ++w) t = add_ck(t, sh.red[w], ovf);
       if (PV) atomic_add_ck(&a.pv[uv], t, ovf);
       if (a.gtotal) atomic_add_ck(&a.gtotal[g], t, ovf);
+      if (a.rooted) a.rooted[a.rooted_pos[oi]] = t;
     }
     if (PV)
       for (uint32_t i = tid; i < d; i += kRootBlock) atomic_add_ck(&a.pv[L[i]], cnt[i], ovf);
@@ -986,7 +987,7 @@ __global__ void __launch_bounds__(kRootBlock, 1) count_block_kernel(CountArgs a)
       const unsigned idx = sh.root;
       __syncthreads();
       if (idx >= a.n_scratch) break;
-      block_root<PV, PA>(a, a.order[idx], slab, slots, tsum, ovf, sh);
+      block_root<PV, PA>(a, a.order[idx], idx, slab, slots, tsum, ovf, sh);
     }
   }
   for (;;) {
@@ -995,7 +996,7 @@ __global__ void __launch_bounds__(kRootBlock, 1) count_block_kernel(CountArgs a)
     const unsigned idx = sh.root;
     __syncthreads();
     if (idx >= a.n_big - a.n_scratch) break;
-    block_root<PV, PA>(a, a.order[a.n_scratch + idx], root_area, slots, tsum, ovf, sh);
+    block_root<PV, PA>(a, a.order[a.n_scratch + idx], a.n_scratch + idx, root_area, slots, tsum, ovf, sh);
   }
   finish_block(a, tsum, ovf, sh.red, kRootWarps);
 }
@@ -1004,8 +1005,8 @@ __global__ void __launch_bounds__(kRootBlock, 1) count_block_kernel(CountArgs a)
 // Roots with d+ <= 64: one warp, rows of one word, items over lanes (arcs for
 // k = 4, triangles u->x_i->x_j for k >= 5, each lane one item).
 template <bool PV, bool PA>
-__device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_t *slot, unsigned long long &tsum_out, unsigned &ovf_out,
-                          unsigned *w_next) {
+__device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32_t oi, uint8_t *slot,
+                                          unsigned long long &tsum_out, unsigned &ovf_out, unsigned *w_next) {
   unsigned ovf = 0;
   unsigned long long tsum = 0;
   const unsigned lane = lane_id();
@@ -1160,10 +1161,11 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint8_
     }
   }
   __syncwarp();
-  if (PV || a.gtotal) {
+  if (PV || a.gtotal || a.rooted) {
     const unsigned long long t = warp_sum64_ck(rsum, ovf);
     if (lane == 0 && PV) atomic_add_ck(&a.pv[uv], t, ovf);
     if (lane == 0 && a.gtotal) atomic_add_ck(&a.gtotal[g], t, ovf);
+    if (lane == 0 && a.rooted) a.rooted[a.rooted_pos[oi]] = t;
     if (PV)
       for (uint32_t i = lane; i < d; i += 32) atomic_add_ck(&a.pv[L[i]], cnt[i], ovf);
   }
@@ -1201,7 +1203,7 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
   uint32_t q = 0, qend = 0, base = 0;
   unsigned mask = 0;
   for (;;) {
-    uint32_t u;
+    uint32_t u, oi = 0;  // oi: position in the order array (out-degree order only)
     if (a.light_by_id) {
       bool done = false;
       while (mask == 0) {
@@ -1241,10 +1243,11 @@ __global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
         q = idx;
         qend = min(nlight, idx + chunk);
       }
-      u = a.order[a.n_big + q];
+      oi = a.n_big + q;
+      u = a.order[oi];
       ++q;
     }
-    warp_root<PV, PA>(a, u, slot, tsum, ovf, &w_next[warp]);
+    warp_root<PV, PA>(a, u, oi, slot, tsum, ovf, &w_next[warp]);
   }
   finish_block(a, tsum, ovf, red, kWarps);
 }

@@ -143,6 +143,10 @@ struct CountArgs {
   const uint64_t *rptr;
   const uint32_t *rcol;
   const uint32_t *rvert;
+  // rooted counts of a root list (null otherwise): the root at position i of
+  // the order array writes its total to rooted[rooted_pos[i]]
+  unsigned long long *rooted;
+  const uint32_t *rooted_pos;
 };
 
 // A configured counting pass (kc_api.cu).
@@ -150,6 +154,8 @@ struct LaunchPlan {
   CountArgs a;
   int block_grid, warp_grid;
   size_t block_smem, scratch_bytes;
+  uint32_t dcap;   // largest out-degree whose root matrix fits shared memory
+  uint32_t light;  // largest out-degree of a warp root
 };
 
 // Process-wide count of kernel launches issued by this library.

@@ -250,6 +250,15 @@ __global__ void degree_from_dag_kernel(const uint64_t *__restrict__ dp, const ui
   }
 }
 
+// out-degree of each listed root (ids already checked to be < n)
+__global__ void root_outdeg_kernel(const uint64_t *__restrict__ dp, const uint32_t *__restrict__ roots, uint32_t r,
+                                   uint32_t *out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < r; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t u = roots[i];
+    out[i] = (uint32_t)(dp[u + 1] - dp[u]);
+  }
+}
+
 // ------------------------------------------------------------- statistics
 // sum over roots of d+(u)^2 and over arcs u->v of d+(v)
 __global__ void __launch_bounds__(kBlock) dag_stats_kernel(const uint64_t *__restrict__ dp,
@@ -329,6 +338,15 @@ cudaError_t launch_outdeg_scatter(const uint64_t *dp, uint32_t n, unsigned *curs
 cudaError_t launch_fill_u64(unsigned long long *out, size_t n, unsigned long long v, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   fill_u64_kernel<<<grid_for(n, kBlock), kBlock, 0, s>>>(out, n, v);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_root_outdeg(const uint64_t *dp, const uint32_t *roots, uint32_t r, uint32_t *out,
+                               cudaStream_t s) {
+  if (r == 0) return cudaSuccess;
+  root_outdeg_kernel<<<grid_for(r, kBlock), kBlock, 0, s>>>(dp, roots, r, out);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -16,6 +16,8 @@ cudaError_t launch_outdeg_hist(const uint64_t *dp, uint32_t n, unsigned *hist, u
 cudaError_t launch_outdeg_scatter(const uint64_t *dp, uint32_t n, unsigned *cursor, uint32_t maxd, uint32_t *order,
                                   cudaStream_t s);
 cudaError_t launch_fill_u64(unsigned long long *out, size_t n, unsigned long long v, cudaStream_t s);
+cudaError_t launch_root_outdeg(const uint64_t *dp, const uint32_t *roots, uint32_t r, uint32_t *out,
+                               cudaStream_t s);
 cudaError_t launch_degree_from_dag(const uint64_t *dp, const uint32_t *dc, uint32_t n, unsigned long long *out,
                                    cudaStream_t s);
 // Sort every out-list by (key, id): order[] lists roots by out-degree,

@@ -115,6 +115,7 @@ def _load():
         lib.kc_count.argtypes = [P, I, ctypes.POINTER(U64), P]
         lib.kc_count_per_vertex.argtypes = [P, I, P, P, P]
         lib.kc_count_per_arc.argtypes = [P, I, P, P, P]
+        lib.kc_count_roots.argtypes = [P, I, P, U32, P, P, P]
         lib.kc_dag_get_stats.argtypes = [P, ctypes.POINTER(_Stats), P]
         BP, PP = ctypes.POINTER(_Batch), ctypes.POINTER(_Params)
         lib.kc_count_batched.argtypes = [P, BP, PP, P, ctypes.POINTER(U64), P]
@@ -153,7 +154,7 @@ def _load():
         lib.kc_last_cuda_error.argtypes = []
         lib.kc_last_cuda_error.restype = ctypes.c_char_p
         for f in (lib.kc_orient, lib.kc_dag_export, lib.kc_count, lib.kc_count_per_vertex,
-                  lib.kc_count_per_arc, lib.kc_dag_get_stats, lib.kc_count_batched, lib.kc_plan_create,
+                  lib.kc_count_per_arc, lib.kc_count_roots, lib.kc_dag_get_stats, lib.kc_count_batched, lib.kc_plan_create,
                   lib.kc_plan_launch, lib.kc_plan_result, lib.kc_autotune_batched):
             f.restype = I
         _lib = lib
@@ -272,6 +273,22 @@ def kc_count_per_arc(dag: Dag, k: int, out: torch.Tensor | None = None, stream=N
     t = ctypes.c_uint64()
     _check(_load().kc_count_per_arc(dag.handle, int(k), out.data_ptr(), ctypes.byref(t), _stream(stream)))
     return int(t.value), out[:dag.m]
+
+
+def kc_count_roots(dag: Dag, k: int, roots: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """(total over the roots, out) with out[i] = k-cliques whose lowest vertex is roots[i]
+    (roots: int32 device tensor of distinct vertex ids; out: int64 storage of uint64)."""
+    _require_cuda(roots, "roots", (torch.int32,))
+    r = roots.numel()
+    if out is None:
+        out = torch.empty(max(r, 1), dtype=torch.int64, device=roots.device)
+    _require_cuda(out, "out", (torch.int64,))
+    if out.numel() < r:
+        raise ValueError("out must have one entry per root")
+    t = ctypes.c_uint64()
+    _check(_load().kc_count_roots(dag.handle, int(k), roots.data_ptr() if r else None, r,
+                                  out.data_ptr(), ctypes.byref(t), _stream(stream)))
+    return int(t.value), out[:r]
 
 
 class Batch:
@@ -497,6 +514,7 @@ orient = kc_orient
 count = kc_count
 count_per_vertex = kc_count_per_vertex
 count_per_arc = kc_count_per_arc
+count_roots = kc_count_roots
 count_batched = kc_count_batched
 peel = kc_peel
 count_colorful = kc_count_colorful

@@ -30,7 +30,7 @@ def lib_path():
 
 def test_header_declares_entry_points():
     names = declared_functions()
-    for must in ("kc_orient", "kc_count", "kc_count_per_vertex", "kc_count_per_arc", "kc_dag_free",
+    for must in ("kc_orient", "kc_count", "kc_count_per_vertex", "kc_count_per_arc", "kc_count_roots", "kc_dag_free",
                  "kc_dag_n", "kc_dag_m", "kc_strerror", "kc_dag_export", "kc_dag_get_stats"):
         assert must in names
 
@@ -77,6 +77,8 @@ def test_binding_checks_arguments_before_any_device_call(lib_path):
         kc.count_colorful(rp, col, 3, 2, 1)
     with pytest.raises(ValueError):
         kc.peel(rp, col, None, 3)
+    with pytest.raises(ValueError):
+        kc.count_roots(None, 4, torch.zeros(3, dtype=torch.int32))
 
 
 def test_binding_constants_match_the_header():

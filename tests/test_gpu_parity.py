@@ -121,6 +121,46 @@ def test_per_arc_bit_exact(kc, graphs, name):
             assert int(pa[e]) == oracle.count_arc(odag, k, int(src[e]), int(col[e])), (name, k, e)
 
 
+@pytest.mark.parametrize("name", ["rmat12", "planted", "turan", "rmat10_dense"])
+def test_rooted_counts_bit_exact(kc, graphs, name):
+    """kc_count_roots: every root's count against the oracle's top call for
+    that root alone (Algorithm 1 from one vertex), on a shuffled root list
+    covering warp, shared-memory and (rmat10_dense at d+ > 64) block roots."""
+    g = graphs[name]
+    dag = gpu_orient(kc, g, "degree")
+    odag = oracle.orient(g, "degree")
+    rng = np.random.default_rng(9)
+    roots = rng.permutation(g.n)[: min(g.n, 1500)]
+    r = torch.from_numpy(roots.astype(np.int32)).cuda()
+    for k in GRAPHS[name][1]:
+        tot, out = kc.count_roots(dag, k, r)
+        want = np.array([oracle.count(odag, k, lo=int(u), hi=int(u) + 1) for u in roots], dtype=np.uint64)
+        np.testing.assert_array_equal(kc.as_uint64(out), want, err_msg=f"{name} k={k}")
+        assert tot == int(want.astype(object).sum())
+
+
+def test_rooted_counts_edges(kc):
+    """All roots sum to the total (including roots in global scratch, K_2100);
+    an empty list; repeated or out-of-range ids are rejected."""
+    g = gg.complete(2100)
+    dag = gpu_orient(kc, g, "degree")
+    every = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    for k in (1, 2, 3, 4):
+        tot, out = kc.count_roots(dag, k, every)
+        out = kc.as_uint64(out)
+        assert tot == math.comb(2100, k) == int(out.astype(object).sum())
+        # the vertex of rank i roots C(2099 - i, k - 1) cliques
+        ptr, _, _ = exported_arcs(dag)
+        dplus = np.diff(ptr.astype(np.int64))
+        assert all(int(out[v]) == math.comb(int(dplus[v]), k - 1) for v in range(0, g.n, 97))
+    tot, out = kc.count_roots(dag, 4, torch.zeros(0, dtype=torch.int32, device="cuda"))
+    assert tot == 0 and out.numel() == 0
+    with pytest.raises(kc.KcError):
+        kc.count_roots(dag, 4, torch.tensor([3, 5, 3], dtype=torch.int32, device="cuda"))
+    with pytest.raises(kc.KcError):
+        kc.count_roots(dag, 4, torch.tensor([3, 2100], dtype=torch.int32, device="cuda"))
+
+
 def test_dag_stats(kc, graphs):
     for name in ("rmat12", "planted", "turan"):
         g = graphs[name]
@@ -239,33 +279,3 @@ def test_config_er2000_full(kc):
         tot, pv = kc.count_per_vertex(dag, k)
         assert tot == want
         np.testing.assert_array_equal(kc.as_uint64(pv), want_pv)
-
-
-def test_config_rmat20_sampled(kc):
-    """R-MAT scale 20: per-arc rooted counts on a seeded sample of arcs against the
-    oracle one arc at a time, plus sum(per-arc) = total and sum(per-vertex) = k total.
-    k = 4, 5 with every output; k = 6 per-arc only (k = 7 is exercised by the bench)."""
-    g = gg.config_rmat20()
-    dag = gpu_orient(kc, g, "degree")
-    ptr, col, src = exported_arcs(dag)
-    # the oracle intersects out-lists sorted by id
-    odag = oracle.Dag(g.n, ptr, np.ascontiguousarray(col[np.lexsort((col, src))]), None)
-    rng = np.random.default_rng(20)
-    pick = rng.choice(odag.m, size=300, replace=False)
-    s3 = {int(e): oracle.count_arc(odag, 3, int(src[e]), int(col[e])) for e in pick}
-    for k in (4, 5, 6):
-        tot, pa = kc.count_per_arc(dag, k)
-        pa = kc.as_uint64(pa)
-        assert int(pa.sum(dtype=np.uint64)) == tot % (1 << 64)
-        if k <= 5:
-            t2, pv = kc.count_per_vertex(dag, k)
-            assert t2 == tot == kc.count(dag, k)
-            assert int(kc.as_uint64(pv).sum(dtype=np.uint64)) == (k * tot) % (1 << 64)
-        checked = 0
-        for e in pick:
-            e = int(e)
-            if k >= 6 and s3[e] > 80:  # keep the oracle within seconds
-                continue
-            assert int(pa[e]) == oracle.count_arc(odag, k, int(src[e]), int(col[e])), (k, e)
-            checked += 1
-        assert checked >= 150

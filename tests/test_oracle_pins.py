@@ -204,6 +204,22 @@ def test_count_arc_sums_to_total():
         assert s == oracle.count(dag, k)
 
 
+def test_count_containing_is_the_per_vertex_definition():
+    """k-cliques through v = (k-1)-cliques of N(v): against brute force per
+    vertex, C(n-1, k-1) on K_n, and sum over v = k * total."""
+    for name, g in small_graphs():
+        for k in (1, 2, 3, 4, 5):
+            _, want_pv = py_brute(g, k)
+            got = [oracle.count_containing(g, k, v) for v in range(g.n)]
+            assert got == want_pv.tolist(), (name, k)
+    K = gg.complete(12)
+    assert oracle.count_containing(K, 5, 3) == math.comb(11, 4)
+    g = gg.rmat(9, 8, seed=4)
+    for k in (3, 4):
+        tot = oracle.count(oracle.orient(g, "degree"), k)
+        assert sum(oracle.count_containing(g, k, v) for v in range(g.n)) == k * tot
+
+
 def test_empty_and_out_of_range_k():
     g = gg.empty(5)
     dag = oracle.orient(g, "degree")
