@@ -146,6 +146,23 @@ kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_
                            kc_stream_t stream);
 
 /*
+ * kc_count_budget -- kc_count (d_out NULL) or kc_count_per_vertex (d_out
+ * device uint64[n]) with a time budget for the pass. (The paper has no
+ * counterpart: a control for callers that serve requests.) The budget starts
+ * when the pass starts on the GPU: a one-thread kernel enqueued on `stream`
+ * just before the counting kernels takes the deadline from the device clock.
+ * Past it the kernels take no new root, item or first-level sub-problem and
+ * the call returns KC_ETIMEDOUT; the partial count is discarded and d_out is
+ * left undefined. A sub-problem already started runs to its end, so a pass
+ * can overrun its budget by one sub-problem.
+ *   budget_us  1 .. 2^63 / 1000 microseconds
+ *   h_total    receives the count when the pass finished in time
+ * Synchronises `stream`. Other status codes as kc_count.
+ */
+kc_status kc_count_budget(const kc_dag *d, int k, uint64_t *d_out, uint64_t budget_us, uint64_t *h_total,
+                          kc_stream_t stream);
+
+/*
  * kc_count_roots -- rooted counts of a list of roots: d_out[i] = number of
  * k-cliques whose lowest vertex in the total order is d_roots[i], i.e. the
  * term that the top call of Algorithm 1 adds for that vertex (every clique is
@@ -466,6 +483,16 @@ kc_status kc_measure_word_op_rate(double *h_rate, kc_stream_t stream);
 /* Number of CUDA kernels this library has launched in this process so far
  * (all entry points, all devices). For accounting in benchmarks. */
 uint64_t kc_kernel_launches(void);
+
+/*
+ * Host-side fault injection for tests (the paper has no counterpart): after
+ * `count` more successful stream-ordered device allocations, every further
+ * one made by this library fails as an out-of-memory error, without calling
+ * CUDA, so that the entry points' KC_ENOMEM paths (and the release of what
+ * they had allocated) can be exercised without exhausting a GPU. count < 0
+ * switches the injection off. Process-wide; for tests only.
+ */
+void kc_debug_fail_allocations_after(int64_t count);
 
 /* Human-readable text for a status code (static storage). */
 const char *kc_strerror(int status);

@@ -23,6 +23,21 @@ namespace kc {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// allocations left before the injected failures start; negative: none injected
+static std::atomic<long long> g_alloc_budget{-1};
+
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+  long long b = g_alloc_budget.load(std::memory_order_relaxed);
+  while (b >= 0) {
+    if (b == 0) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    if (g_alloc_budget.compare_exchange_weak(b, b - 1, std::memory_order_relaxed)) break;
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
 namespace {
 thread_local std::string g_cuda_err;
 }
@@ -71,6 +86,10 @@ const char *kc_last_cuda_error(void) { return kc::g_cuda_err.c_str(); }
 
 uint64_t kc_kernel_launches(void) { return kc::g_launches.load(std::memory_order_relaxed); }
 
+void kc_debug_fail_allocations_after(int64_t count) {
+  kc::g_alloc_budget.store(count < 0 ? -1 : (long long)count, std::memory_order_relaxed);
+}
+
 uint32_t kc_dag_n(const kc_dag *d) { return d ? d->n : 0; }
 uint64_t kc_dag_m(const kc_dag *d) { return d ? d->m : 0; }
 uint32_t kc_dag_max_out_degree(const kc_dag *d) { return d ? d->max_out : 0; }
@@ -117,11 +136,11 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
     if (h_status[0] & kc::ST_BAD_CSR) return KC_EINVAL;
   }
 
-  KC_CK(cudaMallocAsync((void **)&D->ptr, sizeof(uint64_t) * ((size_t)n + 1), s));
+  KC_CK(kc::dev_malloc_async((void **)&D->ptr, sizeof(uint64_t) * ((size_t)n + 1), s));
   if (n == 0) {
     KC_CK(cudaMemsetAsync(D->ptr, 0, sizeof(uint64_t), s));
-    KC_CK(cudaMallocAsync((void **)&D->col, 16, s));
-    KC_CK(cudaMallocAsync((void **)&D->order, 16, s));
+    KC_CK(kc::dev_malloc_async((void **)&D->col, 16, s));
+    KC_CK(kc::dev_malloc_async((void **)&D->order, 16, s));
     D->ge.assign(2, 0);
     KC_CK(cudaStreamSynchronize(s));
     *out = D;
@@ -152,7 +171,7 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   if (h_m != g->nnz / 2) return KC_EINVAL;
   D->m = h_m;
   D->max_out = h_status[1];
-  KC_CK(cudaMallocAsync((void **)&D->col, sizeof(uint32_t) * (h_m ? h_m : 1), s));
+  KC_CK(kc::dev_malloc_async((void **)&D->col, sizeof(uint32_t) * (h_m ? h_m : 1), s));
   KC_CK(kc::launch_write_out(*g, key.as<uint64_t>(), D->ptr, D->col, s));
 
   // roots ordered by out-degree, descending (counting sort)
@@ -169,7 +188,7 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   std::vector<unsigned> start((size_t)maxd + 1);
   for (uint32_t t = 0; t <= maxd; ++t) start[t] = (unsigned)D->ge[t + 1];
   KC_CK(cudaMemcpyAsync(hist.p, start.data(), sizeof(unsigned) * start.size(), cudaMemcpyHostToDevice, s));
-  KC_CK(cudaMallocAsync((void **)&D->order, sizeof(uint32_t) * n, s));
+  KC_CK(kc::dev_malloc_async((void **)&D->order, sizeof(uint32_t) * n, s));
   KC_CK(kc::launch_outdeg_scatter(D->ptr, n, hist.as<unsigned>(), maxd, D->order, s));
   // out-lists into the total order (positions inside N+(u) = ranks among N+(u))
   auto ge = [&](uint64_t t) -> uint32_t { return t < D->ge.size() ? (uint32_t)D->ge[t] : 0u; };
@@ -216,7 +235,16 @@ namespace kc {
 
 size_t kc_work_bytes() { return 64; }
 
-// total at +0, status word at +8, the three root queues at +16
+// A pass with a time budget: the deadline is taken on the device when the
+// pass starts (this kernel runs just before the counting kernels).
+__global__ void stamp_deadline_kernel(unsigned long long *out, unsigned long long budget_ns) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *out = t + budget_ns;
+}
+
+// total at +0, status word at +8, the three root queues at +16, a device
+// deadline at +32
 void set_work(CountArgs *a, uint8_t *w) {
   a->total = (unsigned long long *)w;
   a->status = (unsigned *)(w + 8);
@@ -278,7 +306,7 @@ cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_pa
 
 // Shared driver of kc_count / kc_count_per_vertex / kc_count_per_arc.
 kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned long long *pa, uint64_t *h_total,
-                    uint64_t deadline_ns, cudaStream_t s) {
+                    uint64_t deadline_ns, cudaStream_t s, uint64_t budget_ns) {
   if (!d || k < 1 || k > KC_KMAX) return KC_EINVAL;
   if (pa && k < 2) return KC_EINVAL;
   const uint32_t n = d->n;
@@ -317,6 +345,13 @@ kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned lon
   if (P.scratch_bytes) {
     KC_CK(scratch.alloc(P.scratch_bytes, s));
     a.scratch = scratch.as<uint8_t>();
+  }
+  if (budget_ns) {
+    unsigned long long *dl = (unsigned long long *)(work.as<uint8_t>() + 32);
+    stamp_deadline_kernel<<<1, 1, 0, s>>>(dl, budget_ns);
+    note_launch();
+    KC_CK(cudaGetLastError());
+    a.deadline_dev = dl;
   }
   KC_CK(launch_count(a, pv != nullptr, pa != nullptr, P.block_grid, P.warp_grid, P.block_smem, s));
   unsigned long long h[2] = {0, 0};
@@ -442,6 +477,13 @@ kc_status kc_count_per_vertex(const kc_dag *d, int k, uint64_t *d_out, uint64_t 
 kc_status kc_count_per_arc(const kc_dag *d, int k, uint64_t *d_out, uint64_t *h_total, kc_stream_t stream) {
   if (!d_out) return KC_EINVAL;
   return kc::run_count(d, k, nullptr, (unsigned long long *)d_out, h_total, 0, (cudaStream_t)stream);
+}
+
+kc_status kc_count_budget(const kc_dag *d, int k, uint64_t *d_out, uint64_t budget_us, uint64_t *h_total,
+                          kc_stream_t stream) {
+  if (!h_total || budget_us == 0 || budget_us > (~0ull / 2000ull)) return KC_EINVAL;
+  return kc::run_count(d, k, (unsigned long long *)d_out, nullptr, h_total, 0, (cudaStream_t)stream,
+                       budget_us * 1000ull);
 }
 
 kc_status kc_count_roots(const kc_dag *d, int k, const uint32_t *d_roots, uint32_t num_roots, uint64_t *d_out,

@@ -48,8 +48,8 @@ kc_status kc_plan_create(const kc_dag *d, const kc_batch *b, const kc_params *pr
   p->totals = d_totals;
   p->stream = s;
   cudaError_t e = kc::plan_count(d, b->k_min, false, false, prm, &p->P);
-  if (e == cudaSuccess) e = cudaMallocAsync(&p->work, kc::kc_work_bytes(), s);
-  if (e == cudaSuccess && p->P.scratch_bytes) e = cudaMallocAsync(&p->scratch, p->P.scratch_bytes, s);
+  if (e == cudaSuccess) e = kc::dev_malloc_async(&p->work, kc::kc_work_bytes(), s);
+  if (e == cudaSuccess && p->P.scratch_bytes) e = kc::dev_malloc_async(&p->scratch, p->P.scratch_bytes, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->work, 0, kc::kc_work_bytes(), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {

@@ -158,8 +158,19 @@ __device__ __forceinline__ int plookup(const unsigned long long *tab, uint32_t T
 struct MatView {
   const uint64_t *adj;
   unsigned long long *cnt;  // per-vertex counters (per-vertex only)
+  unsigned *cnt32;          // 32-bit counters used instead of cnt when set
   uint32_t RS, W;
 };
+
+// Adds v to the per-vertex counter of x. The 32-bit counters are used where
+// no entry can reach 2^32 (a root with at most 64 out-neighbours at k <= 10,
+// a compacted item of at most 128 vertices with at most 6 picks); their
+// shared-memory atomics are several times cheaper than 64-bit ones.
+__device__ __forceinline__ void credit(const MatView &V, int x, unsigned long long v) {
+  if (!v) return;
+  if (V.cnt32) atomicAdd(&V.cnt32[x], (unsigned)v);
+  else atomicAdd(&V.cnt[x], v);
+}
 
 template <int G>
 __device__ __forceinline__ unsigned gsum32(unsigned v) {
@@ -244,7 +255,7 @@ __device__ __forceinline__ unsigned long long leaf2(const uint64_t (&C)[NW], con
 #pragma unroll
         for (int r = 0; r < NW; ++r) a += __popcll(C[r] & R[r]);
         a = gsum32<G>(a);
-        if (j == 0 && a) cnt_add(&V.cnt[x], a);
+        if (j == 0) credit(V, x, a);
       } else {
 #pragma unroll
         for (int r = 0; r < NW; ++r) a += __popcll(T[r] & R[r]);
@@ -293,7 +304,7 @@ __device__ __forceinline__ unsigned long long dfs_fixed(const uint64_t (&C)[NW],
         if ((int)c < L - 1) continue;
         const unsigned long long sub = dfs_fixed<G, NW, PV, L - 1>(Cn, V, j, ovf);
         sum = add_ck(sum, sub, ovf);
-        if (PV) cnt_add(&V.cnt[x], sub);
+        if (PV) credit(V, x, sub);
       }
     } else {
       uint64_t T[NW];
@@ -313,7 +324,7 @@ __device__ __forceinline__ unsigned long long dfs_fixed(const uint64_t (&C)[NW],
         if ((int)c < L - 1) continue;
         const unsigned long long sub = dfs_fixed<G, NW, PV, L - 1>(Cn, V, j, ovf);
         sum = add_ck(sum, sub, ovf);
-        if (PV && j == 0) cnt_add(&V.cnt[x], sub);
+        if (PV && j == 0) credit(V, x, sub);
       }
     }
     ovf_out |= ovf;
@@ -383,7 +394,7 @@ __device__ unsigned long long dfs_stack(const uint64_t (&C0)[NW], int ell, const
       }
       --top;
       subs[top] = add_ck(subs[top], a, ovf);
-      if (PV && j == 0) cnt_add(&V.cnt[xs[top]], a);
+      if (PV && j == 0) credit(V, xs[top], a);
     }
   }
   { const auto ret_ = (ret); ovf_out |= ovf; return ret_; }
@@ -493,8 +504,15 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
       bw &= bw - 1;
     }
   }
+  // per-item counters: an entry counts the item's cliques through one of its
+  // s <= 128 vertices, at most C(127, picks - 1), below 2^32 for picks <= 6
+  const bool c32 = picks <= 6;
+  unsigned *cs32 = (unsigned *)sl.cs;
   if (PV)
-    for (uint32_t q = lane; q < s; q += 32) sl.cs[q] = 0;
+    for (uint32_t q = lane; q < s; q += 32) {
+      if (c32) cs32[q] = 0;
+      else sl.cs[q] = 0;
+    }
   __syncwarp();
   const uint32_t NWc = s <= 64 ? 1u : 2u;
   // bit b of compacted row q <=> P[b] adjacent to P[q]
@@ -520,6 +538,7 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
   MatView V;
   V.adj = sl.S;
   V.cnt = sl.cs;
+  V.cnt32 = c32 ? cs32 : nullptr;
   V.RS = NWc;
   V.W = NWc;
   for (uint32_t q = lane; q < s; q += 32) {
@@ -535,7 +554,7 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
       if (picks == 2) sub = (unsigned long long)pc;
       else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, 2, PV>(C, picks - 1, V, 0, ovf);
     }
-    if (PV && picks > 2 && sub) cnt_add(&sl.cs[q], sub);
+    if (PV && picks > 2) credit(V, (int)q, sub);
     acc = add_ck(acc, sub, ovf);
   }
   if (PV && picks == 2) {
@@ -543,12 +562,12 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
     for (uint32_t q = lane; q < s; q += 32) {
       unsigned b = (unsigned)__popcll(sl.S[q * NWc]);
       if (NWc == 2) b += (unsigned)__popcll(sl.S[q * NWc + 1]);
-      if (b) cnt_add(&sl.cs[q], b);
+      credit(V, (int)q, b);
     }
   }
   __syncwarp();
   if (PV)
-    for (uint32_t q = lane; q < s; q += 32) atomic_add_ck(&rc[sl.P[q]], sl.cs[q], ovf);
+    for (uint32_t q = lane; q < s; q += 32) atomic_add_ck(&rc[sl.P[q]], c32 ? cs32[q] : sl.cs[q], ovf);
   const unsigned long long tot = warp_sum64_ck(acc, ovf);
   __syncwarp();
   { const auto ret_ = (tot); ovf_out |= ovf; return ret_; }
@@ -577,7 +596,7 @@ __device__ unsigned long long split_count(const MatView M, uint32_t s, int picks
     unsigned long long sub = 0;
     if (picks == 2) sub = (unsigned long long)pc;
     else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, NW, PV>(C, picks - 1, M, 0, ovf);
-    if (PV && picks > 2 && sub) cnt_add(&M.cnt[x], sub);
+    if (PV && picks > 2) credit(M, (int)x, sub);
     acc = add_ck(acc, sub, ovf);
   }
   if (PV && picks == 2) {
@@ -587,7 +606,7 @@ __device__ unsigned long long split_count(const MatView M, uint32_t s, int picks
       const uint64_t *cy = M.adj + (size_t)y * M.RS;
       unsigned b = 0;
       for (uint32_t w = 0; w < W; ++w) b += (unsigned)__popcll(sl.mask[w] & cy[w]);
-      if (b) cnt_add(&M.cnt[y], b);
+      credit(M, (int)y, b);
     }
   }
   __syncwarp();
@@ -675,8 +694,13 @@ __device__ unsigned long long k4_item(const MatView M, uint32_t s, const Slot sl
 
 // Deadline check (batched and served passes): past the deadline, record
 // ST_TIMEOUT and stop taking roots and items.
+__device__ __forceinline__ uint64_t deadline_of(const CountArgs &a) {
+  return a.deadline_dev ? *a.deadline_dev : a.deadline_ns;  // written before the pass started
+}
+
 __device__ __forceinline__ bool past_deadline(const CountArgs &a) {
-  if (a.deadline_ns && globaltimer_ns() > a.deadline_ns) {
+  const uint64_t dl = deadline_of(a);
+  if (dl && globaltimer_ns() > dl) {
     atomicOr(a.status, ST_TIMEOUT);
     return true;
   }
@@ -737,6 +761,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint3
   }
   if (d + 1 < (uint32_t)k) return;  // the root cannot hold a k-clique
   const uint32_t cmax = a.compact_max ? min(a.compact_max, (uint32_t)kCompactMax) : (uint32_t)kCompactMax;
+  const uint64_t dl = deadline_of(a);
   const RootLayout lay = root_layout(d, PV, PA);
   uint32_t *L = (uint32_t *)(base + lay.L);
   uint64_t *rb = (uint64_t *)(base + lay.rb);
@@ -811,6 +836,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint3
   MatView M;
   M.adj = adj;
   M.cnt = cnt;
+  M.cnt32 = nullptr;
   M.RS = W;
   M.W = W;
   unsigned long long rsum = 0;  // lane 0 of each warp holds its item totals
@@ -876,10 +902,11 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint3
           if (s >= (uint32_t)(k - 2)) {
             if (k == 4) {
               item = k4_item<PV>(M, s, sl, ovf);
-            } else if (k == 5 && (W <= 2 || s > cmax)) {
-              item = split_dispatch<PV>(M, s, 3, sl, ovf, a.deadline_ns, a.status);  // compaction does not pay
+            } else if (k == 5 && (s > cmax || (!PV && W <= 2))) {
+              // count only, rows of at most two words: compaction does not pay
+              item = split_dispatch<PV>(M, s, 3, sl, ovf, dl, a.status);
             } else if (s <= cmax) {
-              item = compact_count<PV>(M, s, k - 2, sl, cnt, ovf, a.deadline_ns, a.status);
+              item = compact_count<PV>(M, s, k - 2, sl, cnt, ovf, dl, a.status);
             }  // else (k >= 6): split into pair items
           }
         }
@@ -910,8 +937,8 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint3
           const uint64_t mw = lane < W ? (wv & rv[lane] & above_word(av, lane)) : 0ull;
           const uint32_t s0 = slot_set(sl, mw, W);
           if (s0 >= (uint32_t)(k - 3)) {
-            if (s0 <= cmax) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf, a.deadline_ns, a.status);
-            else item = split_dispatch<PV>(M, s0, k - 3, sl, ovf, a.deadline_ns, a.status);
+            if (s0 <= cmax) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf, dl, a.status);
+            else item = split_dispatch<PV>(M, s0, k - 3, sl, ovf, dl, a.status);
           }
         } else {
           if (lane == 0) atomicOr(a.status, ST_CAPACITY);
@@ -1091,9 +1118,14 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32
     }
   }
   __syncwarp();
+  // a root with d <= 64 out-neighbours: an entry counts the root's cliques
+  // through one of them, at most C(62, k - 2), below 2^32 for k <= 10
+  const bool c32 = k <= 10;
+  unsigned *cnt32 = (unsigned *)cnt;
   MatView V;
   V.adj = adj;
   V.cnt = cnt;
+  V.cnt32 = (PV && c32) ? cnt32 : nullptr;
   V.RS = 1;
   V.W = 1;
   unsigned long long rsum = 0;
@@ -1102,7 +1134,7 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32
       const uint64_t v = adj[i];
       const unsigned c = (unsigned)__popcll(v & above_word(i, 0));
       rsum = add_ck(rsum, c, ovf);
-      if (PV) cnt[i] = (unsigned)__popcll(v);
+      if (PV) cnt32[i] = (unsigned)__popcll(v);  // k = 3 uses the 32-bit counters
       if (PA) asub[i] = c;
     }
   } else {
@@ -1154,8 +1186,8 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32
       const unsigned long long s = dfs<1, 1, PV>(C, ell, V, 0, ovf);
       rsum = add_ck(rsum, s, ovf);
       if (PV) {
-        cnt_add(&cnt[i], s);
-        if (jv != 0xffffffffu) cnt_add(&cnt[jv], s);
+        credit(V, (int)i, s);
+        if (jv != 0xffffffffu) credit(V, (int)jv, s);
       }
       if (PA) atomic_add_ck(&asub[i], s, ovf);
     }
@@ -1167,7 +1199,7 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32
     if (lane == 0 && a.gtotal) atomic_add_ck(&a.gtotal[g], t, ovf);
     if (lane == 0 && a.rooted) a.rooted[a.rooted_pos[oi]] = t;
     if (PV)
-      for (uint32_t i = lane; i < d; i += 32) atomic_add_ck(&a.pv[L[i]], cnt[i], ovf);
+      for (uint32_t i = lane; i < d; i += 32) atomic_add_ck(&a.pv[L[i]], c32 ? cnt32[i] : cnt[i], ovf);
   }
   if (PA)
     for (uint32_t i = lane; i < d; i += 32) a.pa[b + i] = asub[i];

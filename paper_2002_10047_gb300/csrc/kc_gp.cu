@@ -18,6 +18,7 @@
 
 #include <algorithm>
 
+#include "kc_host.cuh"
 #include "kc_internal.cuh"
 #include "kc_orient.cuh"
 
@@ -143,14 +144,14 @@ kc_status gp_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s) {
   auto ck = [&](cudaError_t x) {
     if (e == cudaSuccess && x != cudaSuccess) e = x;
   };
-  ck(cudaMallocAsync((void **)&deg, sizeof(uint32_t) * n, s));
-  ck(cudaMallocAsync((void **)&la, sizeof(uint32_t) * n, s));
-  ck(cudaMallocAsync((void **)&lb, sizeof(uint32_t) * n, s));
-  ck(cudaMallocAsync((void **)&sel, sizeof(uint32_t) * n, s));
-  ck(cudaMallocAsync((void **)&state, n, s));
+  ck(kc::dev_malloc_async((void **)&deg, sizeof(uint32_t) * n, s));
+  ck(kc::dev_malloc_async((void **)&la, sizeof(uint32_t) * n, s));
+  ck(kc::dev_malloc_async((void **)&lb, sizeof(uint32_t) * n, s));
+  ck(kc::dev_malloc_async((void **)&sel, sizeof(uint32_t) * n, s));
+  ck(kc::dev_malloc_async((void **)&state, n, s));
   // hist[256] + two counters
-  ck(cudaMallocAsync((void **)&hist, sizeof(unsigned) * 260, s));
-  ck(cudaMallocAsync((void **)&st, sizeof(SelectState), s));
+  ck(kc::dev_malloc_async((void **)&hist, sizeof(unsigned) * 260, s));
+  ck(kc::dev_malloc_async((void **)&st, sizeof(SelectState), s));
   if (e == cudaSuccess) {
     gp_init_kernel<<<gp_grid(n), kBlock, 0, s>>>(g.d_row_ptr, n, deg, state, la);
     note_launch();
@@ -185,7 +186,7 @@ kc_status gp_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s) {
   void *bufs[] = {deg, la, lb, sel, state, hist, st};
   for (void *b : bufs)
     if (b) cudaFreeAsync(b, s);
-  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
+  if (e != cudaSuccess) return kc::cuda_fail(e);
   return KC_OK;
 }
 
@@ -238,12 +239,12 @@ kc_status be_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s) {
   auto ck = [&](cudaError_t x) {
     if (e == cudaSuccess && x != cudaSuccess) e = x;
   };
-  ck(cudaMallocAsync((void **)&deg, sizeof(uint32_t) * n, s));
-  ck(cudaMallocAsync((void **)&la, sizeof(uint32_t) * n, s));
-  ck(cudaMallocAsync((void **)&lb, sizeof(uint32_t) * n, s));
-  ck(cudaMallocAsync((void **)&sel, sizeof(uint32_t) * n, s));
-  ck(cudaMallocAsync((void **)&state, n, s));
-  ck(cudaMallocAsync((void **)&cnts, sizeof(unsigned long long) * 3, s));
+  ck(kc::dev_malloc_async((void **)&deg, sizeof(uint32_t) * n, s));
+  ck(kc::dev_malloc_async((void **)&la, sizeof(uint32_t) * n, s));
+  ck(kc::dev_malloc_async((void **)&lb, sizeof(uint32_t) * n, s));
+  ck(kc::dev_malloc_async((void **)&sel, sizeof(uint32_t) * n, s));
+  ck(kc::dev_malloc_async((void **)&state, n, s));
+  ck(kc::dev_malloc_async((void **)&cnts, sizeof(unsigned long long) * 3, s));
   kc_status st = KC_OK;
   // phase 1: the approximate densest subgraph's density rho~ = best_m / best_n
   // phase 2: Barenboim-Elkin rounds with threshold deg < 12 rho~ (eps = 1:
@@ -304,7 +305,7 @@ kc_status be_rank(const kc_csr &g, uint64_t *okey, cudaStream_t s) {
   void *bufs[] = {deg, la, lb, sel, state, cnts};
   for (void *b : bufs)
     if (b) cudaFreeAsync(b, s);
-  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
+  if (e != cudaSuccess) return kc::cuda_fail(e);
   return st;
 }
 

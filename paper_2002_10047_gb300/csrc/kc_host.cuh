@@ -31,7 +31,7 @@ struct DevBuf {
   }
   cudaError_t alloc(size_t bytes, cudaStream_t st) {
     s = st;
-    return cudaMallocAsync(&p, bytes ? bytes : 16, st);
+    return kc::dev_malloc_async(&p, bytes ? bytes : 16, st);
   }
   template <typename T>
   T *as() const {
@@ -50,7 +50,9 @@ struct DevBuf {
 // global scratch the largest roots need (0 if none).
 cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_params *prm, LaunchPlan *P);
 
+// deadline_ns: absolute globaltimer deadline (0 = none); budget_ns: a time
+// budget that starts when the pass starts on the device (0 = none)
 kc_status run_count(const kc_dag *d, int k, unsigned long long *pv, unsigned long long *pa, uint64_t *h_total,
-                    uint64_t deadline_ns, cudaStream_t s);
+                    uint64_t deadline_ns, cudaStream_t s, uint64_t budget_ns = 0);
 
 }  // namespace kc

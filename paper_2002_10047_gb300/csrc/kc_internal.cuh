@@ -121,6 +121,9 @@ struct CountArgs {
   size_t scratch_stride;     // bytes per slab
   uint32_t scratch_blocks;   // blocks that take scratch roots
   uint64_t deadline_ns;      // globaltimer deadline, 0 = none
+  // set for a pass with a time budget: the deadline written on the device by
+  // the kernel that starts the pass (takes the place of deadline_ns)
+  const unsigned long long *deadline_dev;
   // batches of disjoint graphs (null for a single graph): graph g owns
   // vertices [goff[g], goff[g+1]), counts its gk[g]-cliques, sums into gtotal[g]
   const uint64_t *goff;
@@ -160,6 +163,11 @@ struct LaunchPlan {
 
 // Process-wide count of kernel launches issued by this library.
 void note_launch(unsigned n = 1);
+
+// Every stream-ordered device allocation of the library goes through here
+// (cudaMallocAsync, or the injected failure set by
+// kc_debug_fail_allocations_after).
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s);
 
 // Launch helpers implemented in kc_count.cu / kc_orient.cu
 size_t block_root_smem(uint32_t dsmem, bool pv, bool pa);

@@ -46,7 +46,7 @@ extern "C" kc_status kc_measure_word_op_rate(double *h_rate, kc_stream_t stream)
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   unsigned long long *sink = nullptr;
-  if (cudaMallocAsync((void **)&sink, 8, s) != cudaSuccess) return KC_ENOMEM;
+  if (kc::dev_malloc_async((void **)&sink, 8, s) != cudaSuccess) return KC_ENOMEM;
   cudaMemsetAsync(sink, 0, 8, s);
   const int blocks = sms * 8, threads = 256, iters = 1 << 14;
   cudaEvent_t e0, e1;

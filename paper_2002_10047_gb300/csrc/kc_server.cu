@@ -147,10 +147,10 @@ void kc_server::admit(Request &r, int si) {
   kc::CountArgs a = r.plan.a;
   const uint32_t n = r.d->n;
   if (r.pv) {
-    e = cudaMallocAsync((void **)&r.d_pv, sizeof(unsigned long long) * std::max<uint32_t>(n, 1), s.stream);
+    e = kc::dev_malloc_async((void **)&r.d_pv, sizeof(unsigned long long) * std::max<uint32_t>(n, 1), s.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(r.d_pv, 0, sizeof(unsigned long long) * n, s.stream);
   }
-  if (e == cudaSuccess && r.plan.scratch_bytes) e = cudaMallocAsync(&r.scratch, r.plan.scratch_bytes, s.stream);
+  if (e == cudaSuccess && r.plan.scratch_bytes) e = kc::dev_malloc_async(&r.scratch, r.plan.scratch_bytes, s.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.work, 0, kc::kc_work_bytes(), s.stream);
   if (e == cudaSuccess && r.plan.a.n_light_end > 0) {
     kc::set_work(&a, s.work);

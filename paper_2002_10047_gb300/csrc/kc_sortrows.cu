@@ -179,9 +179,9 @@ cudaError_t launch_sort_rows(const uint64_t *ptr, uint32_t *col, const uint64_t 
   uint32_t *gi = nullptr;
   const unsigned grid = n_big < 152 ? n_big : 152;
   if (nmax > kBigMax) {
-    e = cudaMallocAsync((void **)&gk, (size_t)grid * nmax * 8, s);
+    e = kc::dev_malloc_async((void **)&gk, (size_t)grid * nmax * 8, s);
     if (e != cudaSuccess) return e;
-    e = cudaMallocAsync((void **)&gi, (size_t)grid * nmax * 4, s);
+    e = kc::dev_malloc_async((void **)&gi, (size_t)grid * nmax * 4, s);
     if (e != cudaSuccess) {
       cudaFreeAsync(gk, s);
       return e;

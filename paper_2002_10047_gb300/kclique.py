@@ -116,6 +116,7 @@ def _load():
         lib.kc_count_per_vertex.argtypes = [P, I, P, P, P]
         lib.kc_count_per_arc.argtypes = [P, I, P, P, P]
         lib.kc_count_roots.argtypes = [P, I, P, U32, P, P, P]
+        lib.kc_count_budget.argtypes = [P, I, P, U64, ctypes.POINTER(U64), P]
         lib.kc_dag_get_stats.argtypes = [P, ctypes.POINTER(_Stats), P]
         BP, PP = ctypes.POINTER(_Batch), ctypes.POINTER(_Params)
         lib.kc_count_batched.argtypes = [P, BP, PP, P, ctypes.POINTER(U64), P]
@@ -147,6 +148,8 @@ def _load():
         lib.kc_checked_sum.restype = I
         lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         lib.kc_measure_word_op_rate.restype = I
+        lib.kc_debug_fail_allocations_after.argtypes = [ctypes.c_int64]
+        lib.kc_debug_fail_allocations_after.restype = None
         lib.kc_kernel_launches.argtypes = []
         lib.kc_kernel_launches.restype = U64
         lib.kc_strerror.argtypes = [I]
@@ -154,7 +157,7 @@ def _load():
         lib.kc_last_cuda_error.argtypes = []
         lib.kc_last_cuda_error.restype = ctypes.c_char_p
         for f in (lib.kc_orient, lib.kc_dag_export, lib.kc_count, lib.kc_count_per_vertex,
-                  lib.kc_count_per_arc, lib.kc_count_roots, lib.kc_dag_get_stats, lib.kc_count_batched, lib.kc_plan_create,
+                  lib.kc_count_per_arc, lib.kc_count_roots, lib.kc_count_budget, lib.kc_dag_get_stats, lib.kc_count_batched, lib.kc_plan_create,
                   lib.kc_plan_launch, lib.kc_plan_result, lib.kc_autotune_batched):
             f.restype = I
         _lib = lib
@@ -289,6 +292,20 @@ def kc_count_roots(dag: Dag, k: int, roots: torch.Tensor, out: torch.Tensor | No
     _check(_load().kc_count_roots(dag.handle, int(k), roots.data_ptr() if r else None, r,
                                   out.data_ptr(), ctypes.byref(t), _stream(stream)))
     return int(t.value), out[:r]
+
+
+def kc_count_budget(dag: Dag, k: int, budget_us: int, out: torch.Tensor | None = None, stream=None):
+    """A count (out None) or per-vertex count (out: int64 device tensor of n entries) whose pass
+    stops with KcTimeout once budget_us microseconds have passed since it started on the GPU."""
+    ptr = None
+    if out is not None:
+        _require_cuda(out, "out", (torch.int64,))
+        if out.numel() < dag.n:
+            raise ValueError("out must have n entries")
+        ptr = out.data_ptr()
+    t = ctypes.c_uint64()
+    _check(_load().kc_count_budget(dag.handle, int(k), ptr, int(budget_us), ctypes.byref(t), _stream(stream)))
+    return int(t.value)
 
 
 class Batch:
@@ -504,6 +521,12 @@ def kc_measure_word_op_rate(stream=None) -> float:
     return float(r.value)
 
 
+def kc_debug_fail_allocations_after(count: int):
+    """Tests only: the library's device allocations fail (KC_ENOMEM) after `count` more
+    succeed; a negative count switches this off."""
+    _load().kc_debug_fail_allocations_after(int(count))
+
+
 def kc_kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(_load().kc_kernel_launches())
@@ -515,6 +538,7 @@ count = kc_count
 count_per_vertex = kc_count_per_vertex
 count_per_arc = kc_count_per_arc
 count_roots = kc_count_roots
+count_budget = kc_count_budget
 count_batched = kc_count_batched
 peel = kc_peel
 count_colorful = kc_count_colorful
