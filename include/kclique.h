@@ -485,6 +485,17 @@ kc_status kc_measure_word_op_rate(double *h_rate, kc_stream_t stream);
 uint64_t kc_kernel_launches(void);
 
 /*
+ * Process-wide choice of how the counting kernels read the members'
+ * out-lists when they build a block root's induced subgraph (the level-2
+ * build of Section 3.4): enabled != 0 stages them through shared memory with
+ * 1-D bulk copies (cp.async.bulk, two buffers per warp), enabled == 0 (the
+ * default) reads them with ordinary loads, eight in flight per lane, which
+ * measured faster on the GB300. Counts are identical either way; this is a
+ * tunable for measurement. Applies to passes planned after the call.
+ */
+void kc_set_bulk_build(int enabled);
+
+/*
  * Host-side fault injection for tests (the paper has no counterpart): after
  * `count` more successful stream-ordered device allocations, every further
  * one made by this library fails as an out-of-memory error, without calling

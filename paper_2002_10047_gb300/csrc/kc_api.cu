@@ -23,6 +23,9 @@ namespace kc {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+static std::atomic<int> g_bulk_build{0};
+bool bulk_build_enabled() { return g_bulk_build.load(std::memory_order_relaxed) != 0; }
+
 // allocations left before the injected failures start; negative: none injected
 static std::atomic<long long> g_alloc_budget{-1};
 
@@ -56,6 +59,10 @@ int sm_count() {
 }
 
 kc_status status_code(unsigned st) {
+  if (st & ST_STALL) {
+    g_cuda_err = "a bulk copy of the counting kernels did not complete";
+    return KC_ECUDA;
+  }
   if (st & ST_CAPACITY) return KC_ECAPACITY;
   if (st & ST_OVERFLOW) return KC_ERANGE;
   if (st & ST_TIMEOUT) return KC_ETIMEDOUT;
@@ -85,6 +92,8 @@ const char *kc_strerror(int status) {
 const char *kc_last_cuda_error(void) { return kc::g_cuda_err.c_str(); }
 
 uint64_t kc_kernel_launches(void) { return kc::g_launches.load(std::memory_order_relaxed); }
+
+void kc_set_bulk_build(int enabled) { kc::g_bulk_build.store(enabled ? 1 : 0, std::memory_order_relaxed); }
 
 void kc_debug_fail_allocations_after(int64_t count) {
   kc::g_alloc_budget.store(count < 0 ? -1 : (long long)count, std::memory_order_relaxed);
@@ -171,7 +180,8 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   if (h_m != g->nnz / 2) return KC_EINVAL;
   D->m = h_m;
   D->max_out = h_status[1];
-  KC_CK(kc::dev_malloc_async((void **)&D->col, sizeof(uint32_t) * (h_m ? h_m : 1), s));
+  // 16 bytes of padding: bulk copies of an out-list end on a 16-byte boundary
+  KC_CK(kc::dev_malloc_async((void **)&D->col, sizeof(uint32_t) * (h_m + 4), s));
   KC_CK(kc::launch_write_out(*g, key.as<uint64_t>(), D->ptr, D->col, s));
 
   // roots ordered by out-degree, descending (counting sort)
@@ -291,6 +301,7 @@ cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_pa
   a.n = d->n;
   a.light_min = (uint32_t)(k_min - 1);
   a.light_max = light;
+  a.bulk_build = bulk_build_enabled() ? 1u : 0u;
   if (a.n_scratch > 0) {
     const size_t slab = (root_layout(d->max_out, pv, pa).bytes + 255) & ~(size_t)255;
     const size_t sbudget = (size_t)4 << 30;

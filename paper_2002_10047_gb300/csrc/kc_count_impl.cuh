@@ -717,6 +717,143 @@ __device__ __forceinline__ uint32_t graph_of(const CountArgs &a, uint32_t u) {
   return lo;
 }
 
+// ---------------------------------------- bulk-copy staging of the build
+// The level-2 build reads the out-list N+(x) of every member x of N+(u)
+// (Section 3.4). With bulk staging, each warp streams those out-lists into
+// its own slot (idle during the build) with 1-D bulk copies
+// (cp.async.bulk, completion counted by an mbarrier), two buffers deep: the
+// copy of the next segment is in flight while the lanes look up the current
+// one in shared memory. A copy starts and ends on 16-byte boundaries, so a
+// segment is widened by up to three entries on each side (the DAG's column
+// array carries 16 bytes of padding) and the lanes skip the extra entries.
+constexpr int kBuildUnroll = 8;            // entries per lane per pass of the build
+constexpr unsigned kWaitTries = 1u << 24;  // bound of an mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Waits (bounded) for the phase of the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, unsigned parity) {
+  for (unsigned it = 0; it < kWaitTries; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// One lane: expect `bytes` on the mbarrier and start the copy global -> shared.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// The rows N+(L[i]) (start rb[i], length rl[i]) pulled from `next`, staged
+// through the warp's slot and handed to mark(i, entries) kBuildUnroll * 32
+// entries at a time (kEmpty past the segment). Called by all lanes.
+template <typename Mark>
+__device__ __forceinline__ void build_rows_bulk(const CountArgs &a, uint32_t d, const uint64_t *rb, const uint32_t *rl,
+                                                uint8_t *slot, size_t slot_bytes, unsigned &next, Mark &mark) {
+  const unsigned lane = lane_id();
+  uint64_t *mb = (uint64_t *)slot;  // two mbarriers, then the two buffers
+  // each buffer a multiple of 16 bytes; a segment leaves room for the widening
+  const uint32_t cap = (uint32_t)(((slot_bytes - 16) / 2) / 16) * 4;
+  const uint32_t seg = cap - 8;
+  uint32_t *buf[2];
+  buf[0] = (uint32_t *)(slot + 16);
+  buf[1] = buf[0] + cap;
+  const uint32_t mbar[2] = {smem_addr(&mb[0]), smem_addr(&mb[1])};
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar[0]) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar[1]) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncwarp();
+  unsigned parity[2] = {0u, 0u};
+  uint32_t ri[2], rn[2], roff[2];  // row, entries and first-entry offset of each buffer's segment
+  uint32_t cur_i = 0xffffffffu, cur_e = 0, cur_len = 0;
+  uint64_t cur_xb = 0;
+  // the next segment: the rest of the current row, or the next row with entries
+  auto next_seg = [&](uint32_t &i, uint32_t &e0, uint32_t &ne, uint64_t &xb) -> bool {
+    while (cur_i == 0xffffffffu || cur_e >= cur_len) {
+      unsigned r = 0;
+      if (lane == 0) r = atomicAdd(&next, 1u);
+      r = __shfl_sync(0xffffffffu, r, 0);
+      if (r >= d) return false;
+      cur_i = r;
+      cur_e = 0;
+      cur_len = rl[r];
+      cur_xb = rb[r];
+    }
+    i = cur_i;
+    e0 = cur_e;
+    ne = min(seg, cur_len - cur_e);
+    xb = cur_xb;
+    cur_e += ne;
+    return true;
+  };
+  auto issue = [&](int b, uint32_t i, uint32_t e0, uint32_t ne, uint64_t xb) {
+    const uint64_t first = xb + e0, start = first & ~3ull, end = (first + ne + 3) & ~3ull;
+    ri[b] = i;
+    rn[b] = ne;
+    roff[b] = (uint32_t)(first - start);
+    if (lane == 0) bulk_copy(smem_addr(buf[b]), a.col + start, (uint32_t)(end - start) * 4u, mbar[b]);
+  };
+  uint32_t i0, e0, n0;
+  uint64_t x0;
+  bool have = next_seg(i0, e0, n0, x0);
+  if (have) issue(0, i0, e0, n0, x0);
+  int b = 0;
+  bool ok = true;
+  while (have) {
+    uint32_t i1, e1, n1;
+    uint64_t x1;
+    const bool have_next = next_seg(i1, e1, n1, x1);
+    if (have_next) issue(1 - b, i1, e1, n1, x1);
+    if (!mbar_wait(mbar[b], parity[b])) {
+      ok = false;
+      break;
+    }
+    parity[b] ^= 1u;
+    const uint32_t *src = buf[b] + roff[b];
+    for (uint32_t base = 0; base < rn[b]; base += 32 * kBuildUnroll) {
+      uint32_t y[kBuildUnroll];
+#pragma unroll
+      for (int q = 0; q < kBuildUnroll; ++q) {
+        const uint32_t e = base + lane + 32 * q;
+        y[q] = e < rn[b] ? src[e] : kEmpty;
+      }
+      mark(ri[b], y);
+    }
+    __syncwarp();  // every lane is done with buffer b before it is refilled
+    b = 1 - b;
+    have = have_next;
+  }
+  if (!ok) {
+    // a copy did not complete in time: report it, and wait (bounded) for the
+    // copies still in flight before the slot is used for anything else
+    if (lane == 0) atomicOr(a.status, ST_STALL);
+    mbar_wait(mbar[0], parity[0]);
+    mbar_wait(mbar[1], parity[1]);
+  }
+  __syncwarp();
+  if (lane == 0) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mbar[0]) : "memory");
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(mbar[1]) : "memory");
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------- block-level root
 struct BlockShared {
   unsigned long long red[kRootWarps];
@@ -791,44 +928,50 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint3
   __syncthreads();
   for (uint32_t i = tid; i < d; i += kRootBlock) pinsert(tab, T, L[i], i);
   __syncthreads();
-  // the induced subgraph on N+(u): warps take whole rows (row i = N+(L[i]));
-  // eight loads in flight per lane. Out-lists are in rank order, so the hits
-  // of one row arrive in increasing position and the row's bits are set with
-  // one atomic per distinct word.
-  for (;;) {
-    unsigned i = 0;
-    if (lane == 0) i = atomicAdd(&sh.next, 1u);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= d) break;
-    const uint64_t xb = rb[i];
-    const uint32_t len = rl[i];
-    constexpr int U = 8;
-    for (uint32_t base = 0; base < len; base += 32 * U) {
-      uint32_t y[U];
+  // the induced subgraph on N+(u): warps take whole rows (row i = N+(L[i])).
+  // Out-lists are in rank order, so the hits of one row arrive in increasing
+  // position and the row's bits are set with one atomic per distinct word.
+  auto mark = [&](uint32_t i, const uint32_t (&y)[kBuildUnroll]) {
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const uint32_t e = base + lane + 32 * q;
-        y[q] = e < len ? a.col[xb + e] : kEmpty;
+    for (int q = 0; q < kBuildUnroll; ++q) {
+      const int t = y[q] == kEmpty ? -1 : plookup(tab, T, y[q]);
+      const bool hit = t >= 0;
+      const uint32_t w = hit ? ((uint32_t)t >> 6) : 0u;
+      unsigned todo = __ballot_sync(0xffffffffu, hit);
+      while (todo) {
+        const int ld = __ffs(todo) - 1;
+        const uint32_t wl = __shfl_sync(0xffffffffu, w, ld);
+        const bool mine = hit && w == wl;
+        const uint64_t bit = mine ? (1ull << (t & 63)) : 0ull;
+        const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)bit);
+        const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(bit >> 32));
+        if (lane == (unsigned)ld)
+          atomicOr((unsigned long long *)&adj[(size_t)i * W + wl], ((unsigned long long)hi << 32) | lo);
+        todo &= ~__ballot_sync(0xffffffffu, mine);
       }
+      // the lower triangle is read only by the per-vertex credits
+      if (PV && hit) atomicOr((unsigned long long *)&adj[(size_t)t * W + (i >> 6)], 1ull << (i & 63));
+    }
+  };
+  if (a.bulk_build) {
+    build_rows_bulk(a, d, rb, rl, slots + (size_t)warp * slot_layout(PV).bytes, slot_layout(PV).bytes, sh.next, mark);
+  } else {
+    // eight loads in flight per lane
+    for (;;) {
+      unsigned i = 0;
+      if (lane == 0) i = atomicAdd(&sh.next, 1u);
+      i = __shfl_sync(0xffffffffu, i, 0);
+      if (i >= d) break;
+      const uint64_t xb = rb[i];
+      const uint32_t len = rl[i];
+      for (uint32_t base = 0; base < len; base += 32 * kBuildUnroll) {
+        uint32_t y[kBuildUnroll];
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int t = y[q] == kEmpty ? -1 : plookup(tab, T, y[q]);
-        const bool hit = t >= 0;
-        const uint32_t w = hit ? ((uint32_t)t >> 6) : 0u;
-        unsigned todo = __ballot_sync(0xffffffffu, hit);
-        while (todo) {
-          const int ld = __ffs(todo) - 1;
-          const uint32_t wl = __shfl_sync(0xffffffffu, w, ld);
-          const bool mine = hit && w == wl;
-          const uint64_t bit = mine ? (1ull << (t & 63)) : 0ull;
-          const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)bit);
-          const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(bit >> 32));
-          if (lane == (unsigned)ld)
-            atomicOr((unsigned long long *)&adj[(size_t)i * W + wl], ((unsigned long long)hi << 32) | lo);
-          todo &= ~__ballot_sync(0xffffffffu, mine);
+        for (int q = 0; q < kBuildUnroll; ++q) {
+          const uint32_t e = base + lane + 32 * q;
+          y[q] = e < len ? a.col[xb + e] : kEmpty;
         }
-        // the lower triangle is read only by the per-vertex credits
-        if (PV && hit) atomicOr((unsigned long long *)&adj[(size_t)t * W + (i >> 6)], 1ull << (i & 63));
+        mark(i, y);
       }
     }
   }

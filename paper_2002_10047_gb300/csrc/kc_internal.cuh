@@ -14,6 +14,7 @@ enum : unsigned {
   ST_TIMEOUT = 4u,    // deadline / cancel
   ST_CAPACITY = 8u,   // an internal capacity check failed (the access was skipped)
   ST_BAD_ARG = 16u,   // a per-graph k of a batch outside [3, KC_KMAX]
+  ST_STALL = 32u,     // a bulk copy did not complete within its bounded wait
 };
 
 constexpr int kBlock = 256;              // threads per block of the orientation kernels
@@ -124,6 +125,9 @@ struct CountArgs {
   // set for a pass with a time budget: the deadline written on the device by
   // the kernel that starts the pass (takes the place of deadline_ns)
   const unsigned long long *deadline_dev;
+  // level-2 build of block roots: stage the members' out-lists with bulk
+  // copies (kc_set_bulk_build)
+  uint32_t bulk_build;
   // batches of disjoint graphs (null for a single graph): graph g owns
   // vertices [goff[g], goff[g+1]), counts its gk[g]-cliques, sums into gtotal[g]
   const uint64_t *goff;
@@ -163,6 +167,9 @@ struct LaunchPlan {
 
 // Process-wide count of kernel launches issued by this library.
 void note_launch(unsigned n = 1);
+
+// Process-wide choice of the block-root build: bulk-copy staging or direct loads.
+bool bulk_build_enabled();
 
 // Every stream-ordered device allocation of the library goes through here
 // (cudaMallocAsync, or the injected failure set by

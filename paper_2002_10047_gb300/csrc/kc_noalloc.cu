@@ -106,6 +106,7 @@ extern "C" kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total,
   a.n_light_end = ge(need);
   a.n_big = ge(kc::kLightMax + 1);
   a.n_scratch = ge((uint64_t)dcap + 1);
+  a.bulk_build = kc::bulk_build_enabled() ? 1u : 0u;
   uint8_t *b = (uint8_t *)base;
   a.total = (unsigned long long *)b;
   a.status = (unsigned *)(b + 8);

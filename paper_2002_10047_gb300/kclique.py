@@ -148,6 +148,8 @@ def _load():
         lib.kc_checked_sum.restype = I
         lib.kc_measure_word_op_rate.argtypes = [ctypes.POINTER(ctypes.c_double), P]
         lib.kc_measure_word_op_rate.restype = I
+        lib.kc_set_bulk_build.argtypes = [ctypes.c_int]
+        lib.kc_set_bulk_build.restype = None
         lib.kc_debug_fail_allocations_after.argtypes = [ctypes.c_int64]
         lib.kc_debug_fail_allocations_after.restype = None
         lib.kc_kernel_launches.argtypes = []
@@ -519,6 +521,12 @@ def kc_measure_word_op_rate(stream=None) -> float:
     r = ctypes.c_double()
     _check(_load().kc_measure_word_op_rate(ctypes.byref(r), _stream(stream)))
     return float(r.value)
+
+
+def kc_set_bulk_build(enabled: bool):
+    """Block-root builds stage the members' out-lists with bulk copies (True) or read them
+    with ordinary loads (False, the default); counts are identical."""
+    _load().kc_set_bulk_build(1 if enabled else 0)
 
 
 def kc_debug_fail_allocations_after(count: int):
