@@ -573,6 +573,9 @@ __device__ unsigned long long compact_count(const MatView M, uint32_t s, int pic
   { const auto ret_ = (tot); ovf_out |= ovf; return ret_; }
 }
 
+// root positions that the slot's S and cs areas hold 32-bit counters for
+constexpr uint32_t kSplitLocal = (kCompactMax * 2 * 8 + kCompactMax * 8) / 4;
+
 // Lanes split the first pick of the slot's set (root positions, W <= NW <= 32
 // words) and each lane runs the recursion on the root matrix with NW-word sets
 // in registers. Returns the warp-uniform total.
@@ -583,6 +586,18 @@ __device__ unsigned long long split_count(const MatView M, uint32_t s, int picks
   const unsigned lane = lane_id();
   const uint32_t W = M.W;
   unsigned long long acc = 0;
+  // per vertex with three picks: the credits go to 32-bit counters in the
+  // warp's slot (the S and cs areas, 768 root positions; an entry is at most
+  // C(s - 1, 2) < 2^32) and from there once to the root's counters
+  MatView V = M;
+  unsigned *lc = (unsigned *)sl.S;
+  const bool local = PV && picks == 3 && W * 64 <= kSplitLocal;
+  if (local) {
+    for (uint32_t w = lane; w < W; w += 32)
+      for (uint64_t b = sl.mask[w]; b; b &= b - 1) lc[w * 64 + __ffsll((long long)b) - 1] = 0u;
+    __syncwarp();
+    V.cnt32 = lc;
+  }
   for (uint32_t r = lane; r < s; r += 32) {
     const uint32_t x = slot_select(sl, W, r);
     const uint64_t *rx = M.adj + (size_t)x * M.RS;
@@ -595,10 +610,19 @@ __device__ unsigned long long split_count(const MatView M, uint32_t s, int picks
     }
     unsigned long long sub = 0;
     if (picks == 2) sub = (unsigned long long)pc;
-    else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, NW, PV>(C, picks - 1, M, 0, ovf);
-    if (PV && picks > 2) credit(M, (int)x, sub);
+    else if (pc >= picks - 1 && !lane_past(dl_ns, dl_status)) sub = dfs<1, NW, PV>(C, picks - 1, V, 0, ovf);
+    if (PV && picks > 2) credit(V, (int)x, sub);
     acc = add_ck(acc, sub, ovf);
   }
+  if (local) {
+    __syncwarp();
+    for (uint32_t w = lane; w < W; w += 32)
+      for (uint64_t b = sl.mask[w]; b; b &= b - 1) {
+        const uint32_t x = w * 64 + __ffsll((long long)b) - 1;
+        atomic_add_ck(&M.cnt[x], lc[x], ovf);
+      }
+  }
+
   if (PV && picks == 2) {
     // each arc inside the set is one clique: v lies on |set & adj[v]| of them
     for (uint32_t r = lane; r < s; r += 32) {
