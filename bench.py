@@ -36,6 +36,12 @@ sys.path.insert(0, ROOT)
 METRIC = "k-cliques counted/sec"
 UNIT = "cliques/s"
 WORKLOAD = "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 2; orient + total and per-vertex counts"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the block kernel of the k = 6 per-vertex pass on this workload, from a
+# one-pass ncu capture of the kernels as they stand
+# (profiles/count_block_kernel_k6_pervertex_rmat18.md); the warp kernel's
+# share of that pass is under 2% of its time
+TRAFFIC_K6_PV = 59.45e6 + 7.37e6
 
 
 def parse():
@@ -641,7 +647,9 @@ def run_ours(args, rank, world):
         roofline = {"bound": "alu", "kernel": f"count_block_kernel + count_warp_kernel, per-vertex, k={dom}",
                     "achieved": ach / 1e9, "peak": rate / 1e9, "unit": "Gwordop/s",
                     "peak_source": "measured (calibration kernel, 64-bit AND + popcount, this GPU)",
-                    "nominal_peak": nominal / 1e9, "frac": ach / rate, "traffic": None,
+                    "nominal_peak": nominal / 1e9, "frac": ach / rate,
+                    "traffic": TRAFFIC_K6_PV if (dom == 6 and args.scale == 20) else None,
+                    "traffic_note": "DRAM bytes per launch of the block kernel (ncu, 1 pass, this workload)",
                     "alg_word_ops_per_launch": per_k[str(dom)]["alg_word_ops"],
                     "alg_word_ops_x_root_width": ops_w, "achieved_x_root_width": ach_w / 1e9,
                     "frac_x_root_width": ach_w / rate}
