@@ -38,9 +38,8 @@ UNIT = "cliques/s"
 WORKLOAD = "R-MAT scale 20, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), seed 2; orient + total and per-vertex counts"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the block kernel of the k = 6 per-vertex pass on this workload, from a
-# one-pass ncu capture of the kernels as they stand
-# (profiles/count_block_kernel_k6_pervertex_rmat18.md); the warp kernel's
-# share of that pass is under 2% of its time
+# one-pass ncu capture of the kernels as they stand; the warp kernel's share
+# of that pass is under 2% of its time
 TRAFFIC_K6_PV = 59.45e6 + 7.37e6
 
 
