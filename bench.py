@@ -1659,7 +1659,7 @@ def run_peel(args, rank, world):
         "config": {"workload": peel_workload(args), "n": g.n, "m": g.m, "k": args.peel_k},
         "peel": res, "best_density": res["best_cliques"] / max(1, res["best_vertices"]),
         "rounds_per_s": res["rounds"] / (t_max / 1e3), "approx_peel": approx, "clocks": clk.summary(),
-        "note": "one host synchronisation per round (the next round's set depends on this round's counts)",
+        "note": "two host synchronisations per round (the round set and the sizes of its candidate rows are read back; the next round depends on this one)",
     }
     if not args.no_cpu_baseline:
         r, done, rounds, dt = oracle_peel_rate(g, args.peel_k, args.cpu_seconds)

@@ -144,6 +144,19 @@ __global__ void peel_apply_kernel(unsigned long long *__restrict__ C, unsigned l
   }
 }
 
+// end of a round's Update: the cliques it removed and its counting pass's
+// status go to the peel's running totals, read back with the next round's
+// |A| (one host synchronisation fewer per round)
+__global__ void peel_epilogue_kernel(const unsigned long long *__restrict__ cwork, unsigned long long *removed,
+                                     unsigned *status) {
+  const unsigned long long t = cwork[0];
+  const unsigned long long old = *removed;
+  *removed = old + t;
+  unsigned st = (unsigned)cwork[1];
+  if (old + t < old) st |= ST_OVERFLOW;
+  if (st) *status |= st;
+}
+
 unsigned grid_for(size_t work, int block) {
   size_t g = (work + block - 1) / block;
   g = std::max<size_t>(1, std::min<size_t>(g, (size_t)sm_count() * 32));
@@ -183,7 +196,7 @@ kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_
   KC_CK(rorder.alloc(sizeof(uint32_t) * n, s));
   const size_t te = scan_tmp_elems(n);
   KC_CK(scan_tmp.alloc(sizeof(uint64_t) * te, s));
-  KC_CK(work.alloc(64, s));  // min @0, |A| @8, max |I| @12, status @16
+  KC_CK(work.alloc(64, s));  // min @0, |A| @8, max |I| @12, status @16, cliques removed @24
   // per-round buffers, sized once: the length histogram (|I(v)| <= the
   // largest degree), the counting pass's work block, and global scratch
   // grown on demand for rows too long for shared memory
@@ -205,9 +218,10 @@ kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_
   uint8_t *w = work.as<uint8_t>();
   unsigned long long *d_min = (unsigned long long *)w;
   unsigned *d_nA = (unsigned *)(w + 8), *d_maxlen = (unsigned *)(w + 12), *d_status = (unsigned *)(w + 16);
+  unsigned long long *d_removed = (unsigned long long *)(w + 24);  // cliques removed by all Updates so far
   KC_CK(cudaMemsetAsync(dec.p, 0, sizeof(unsigned long long) * n, s));
   KC_CK(cudaMemsetAsync(d_round, 0xff, sizeof(uint32_t) * n, s));
-  KC_CK(cudaMemsetAsync(w + 16, 0, 4, s));
+  KC_CK(cudaMemsetAsync(w + 16, 0, 16, s));
 
   // the seed: per-vertex counts of the whole graph (arb-count-v)
   uint64_t total = 0;
@@ -217,9 +231,39 @@ kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_
   uint64_t t_rem = total, f = 0;
   uint64_t best_num = total, best_den = n;
   uint32_t best_rounds = 0, r = 0;
+  std::vector<unsigned> start;
+  // the round whose Update's result is read back with the next round's |A|
+  bool pending = false;
+  uint64_t pending_f = 0;
+  struct Readback {
+    unsigned long long min;
+    unsigned nA, maxlen, status, pad;
+    unsigned long long removed;
+  } hw{};
+  // applies a readback: the removed cliques of the rounds so far give the
+  // remaining count, and the pending round's density is compared
+  auto settle = [&]() -> kc_status {
+    const kc_status cs = status_code(hw.status);
+    if (cs != KC_OK) return cs;
+    if (hw.removed > total) return KC_ECUDA;  // removed more cliques than there were: cannot happen
+    t_rem = total - hw.removed;
+    if (pending) {
+      if (pending_f < n && frac_gt(t_rem, best_den, best_num, n - pending_f)) {
+        best_num = t_rem;
+        best_den = n - pending_f;
+        best_rounds = r;
+      }
+      pending = false;
+    }
+    return KC_OK;
+  };
   while (f < n) {
     KC_CK(cudaMemsetAsync(w + 8, 0, 8, s));
     if (approx) {
+      // the threshold needs the remaining count now
+      KC_CK(cudaMemcpyAsync(&hw, w, sizeof hw, cudaMemcpyDeviceToHost, s));
+      KC_CK(cudaStreamSynchronize(s));
+      if ((st = settle()) != KC_OK) return st;
       // threshold floor(k (1 + eps) t / |S|) with S the remaining vertices,
       // exact in 128-bit integers: k (den + num) t / (|S| den)
       const unsigned __int128 num = (unsigned __int128)(uint64_t)k * (eps_den + eps_num) * t_rem;
@@ -236,9 +280,11 @@ kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_
                                                                       0ull, r, A.as<uint32_t>(), d_nA);
       note_launch();
     }
-    unsigned h_nA = 0;
-    KC_CK(cudaMemcpyAsync(&h_nA, d_nA, 4, cudaMemcpyDeviceToHost, s));
+    // |A|, and the cliques removed by the Updates so far (the last round's too)
+    KC_CK(cudaMemcpyAsync(&hw, w, sizeof hw, cudaMemcpyDeviceToHost, s));
     KC_CK(cudaStreamSynchronize(s));
+    if ((st = settle()) != KC_OK) return st;
+    const unsigned h_nA = hw.nA;
     if (h_nA == 0) return KC_ECUDA;  // no live vertex found although f < n: cannot happen
     f += h_nA;
     if (t_rem > 0) {
@@ -247,26 +293,27 @@ kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_
           g->d_row_ptr, g->d_col, d->key, d_round, A.as<uint32_t>(), h_nA, r, len.as<uint32_t>(), d_maxlen);
       note_launch();
       KC_CK(exclusive_scan_u32(len.as<uint32_t>(), rptr.as<uint64_t>(), h_nA, scan_tmp.as<uint64_t>(), te, s));
+      // the rows and the histogram of their lengths (|I(v)| <= the largest
+      // degree) before the one read-back of the sizes
+      peel_fill_kernel<<<grid_for((size_t)h_nA * 32, kPeelBlock), kPeelBlock, 0, s>>>(
+          g->d_row_ptr, g->d_col, d->key, d_round, A.as<uint32_t>(), h_nA, r, rptr.as<uint64_t>(),
+          rcol.as<uint32_t>());
+      note_launch();
+      KC_CK(cudaMemsetAsync(hist.p, 0, sizeof(unsigned) * ((size_t)maxdeg + 1), s));
+      KC_CK(launch_outdeg_hist(rptr.as<uint64_t>(), h_nA, hist.as<unsigned>(), maxdeg, s));
       uint64_t h_nr = 0;
       unsigned h_maxlen = 0;
+      std::vector<unsigned> h_hist((size_t)maxdeg + 1);
       KC_CK(cudaMemcpyAsync(&h_nr, rptr.as<uint64_t>() + h_nA, 8, cudaMemcpyDeviceToHost, s));
       KC_CK(cudaMemcpyAsync(&h_maxlen, d_maxlen, 4, cudaMemcpyDeviceToHost, s));
+      KC_CK(cudaMemcpyAsync(h_hist.data(), hist.p, sizeof(unsigned) * h_hist.size(), cudaMemcpyDeviceToHost, s));
       KC_CK(cudaStreamSynchronize(s));
       if (h_nr > g->nnz) return KC_ECUDA;
+      if (h_maxlen > maxdeg) return KC_ECUDA;  // |I(v)| <= deg(v): cannot happen
       if (h_maxlen + 1 >= (unsigned)k && h_nr > 0) {
         if (h_maxlen > KC_MAX_OUT_DEGREE) return KC_ECAPACITY;
-        peel_fill_kernel<<<grid_for((size_t)h_nA * 32, kPeelBlock), kPeelBlock, 0, s>>>(
-            g->d_row_ptr, g->d_col, d->key, d_round, A.as<uint32_t>(), h_nA, r, rptr.as<uint64_t>(),
-            rcol.as<uint32_t>());
-        note_launch();
         // rows by length, descending (the counting kernels' root order), then
         // each row into rank order
-        if (h_maxlen > maxdeg) return KC_ECUDA;  // |I(v)| <= deg(v): cannot happen
-        KC_CK(cudaMemsetAsync(hist.p, 0, sizeof(unsigned) * ((size_t)h_maxlen + 1), s));
-        KC_CK(launch_outdeg_hist(rptr.as<uint64_t>(), h_nA, hist.as<unsigned>(), h_maxlen, s));
-        std::vector<unsigned> h_hist((size_t)h_maxlen + 1);
-        KC_CK(cudaMemcpyAsync(h_hist.data(), hist.p, sizeof(unsigned) * h_hist.size(), cudaMemcpyDeviceToHost, s));
-        KC_CK(cudaStreamSynchronize(s));
         kc_dag rows;  // the round's rows in the shape the planner reads
         rows.n = n;
         rows.m = h_nr;
@@ -276,7 +323,9 @@ kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_
         rows.order = rorder.as<uint32_t>();
         rows.ge.assign((size_t)h_maxlen + 2, 0);
         for (int64_t t = h_maxlen; t >= 0; --t) rows.ge[t] = rows.ge[t + 1] + h_hist[t];
-        std::vector<unsigned> start((size_t)h_maxlen + 1);
+        // `start` outlives the copy: it is rewritten only after the next
+        // read-back, which completes after every earlier copy on the stream
+        start.assign((size_t)h_maxlen + 1, 0u);
         for (uint32_t t = 0; t <= h_maxlen; ++t) start[t] = (unsigned)rows.ge[t + 1];
         KC_CK(cudaMemcpyAsync(hist.p, start.data(), sizeof(unsigned) * start.size(), cudaMemcpyHostToDevice, s));
         KC_CK(launch_outdeg_scatter(rptr.as<uint64_t>(), h_nA, hist.as<unsigned>(), h_maxlen, rorder.as<uint32_t>(), s));
@@ -305,24 +354,20 @@ kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_
             C.as<unsigned long long>(), dec.as<unsigned long long>(), d_round, rcol.as<uint32_t>(), h_nr,
             A.as<uint32_t>(), h_nA, d_status);
         note_launch();
-        unsigned long long h[2] = {0, 0};
-        unsigned h_st = 0;
-        KC_CK(cudaMemcpyAsync(h, cwork.p, sizeof h, cudaMemcpyDeviceToHost, s));
-        KC_CK(cudaMemcpyAsync(&h_st, d_status, 4, cudaMemcpyDeviceToHost, s));
-        KC_CK(cudaStreamSynchronize(s));  // also orders the pageable `start` copy
-        const kc_status cs = status_code((unsigned)h[1] | h_st);
-        if (cs != KC_OK) return cs;
-        if (h[0] > t_rem) return KC_ECUDA;  // removed more cliques than remain: cannot happen
-        t_rem -= h[0];
+        peel_epilogue_kernel<<<1, 1, 0, s>>>(cwork.as<unsigned long long>(), d_removed, d_status);
+        note_launch();
+        KC_CK(cudaGetLastError());
       }
     }
-    if (f < n && frac_gt(t_rem, best_den, best_num, n - f)) {
-      best_num = t_rem;
-      best_den = n - f;
-      best_rounds = r + 1;
-    }
     ++r;
+    pending = true;
+    pending_f = f;
+    if (f >= n) break;
   }
+  // the last round's Update
+  KC_CK(cudaMemcpyAsync(&hw, w, sizeof hw, cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  if ((st = settle()) != KC_OK) return st;
   out->rounds = r;
   out->best_rounds = best_rounds;
   out->best_cliques = best_num;
