@@ -58,6 +58,8 @@ typedef enum {
                               subgraph's density (removal rounds at degree <= 4 * density) */
 /* Flags or-ed into `method`: */
 #define KC_VALIDATE_SYMMETRY 0x100 /* also check that every arc u->v has v->u */
+#define KC_CORE_BITS 0x200         /* always build the dense-core bit matrix (see kc_set_core_policy) */
+#define KC_NO_CORE_BITS 0x400      /* never build it (default: built where it pays, see below) */
 
 /*
  * Simple undirected graph in CSR form (Section 2, "Graph Storage").
@@ -88,12 +90,45 @@ typedef struct kc_dag kc_dag;
  * filter", end of Section 3.1).
  *   g       the input CSR (device arrays)
  *   method  KC_ORIENT_DEGREE, KC_ORIENT_GP or KC_ORIENT_BE, optionally | KC_VALIDATE_SYMMETRY
+ *           and | KC_CORE_BITS or | KC_NO_CORE_BITS (not both)
  *   out     receives a new handle on success (*out untouched on error)
  * The CSR is validated first (ascending rows, no self-loops, ids < n,
  * row_ptr consistent; symmetry on request): a violation gives KC_EINVAL.
  * Synchronises `stream`. Free the handle with kc_dag_free.
+ *
+ * Dense core (a layout of the DAG; the paper has no counterpart). The
+ * induced-subgraph build of a root u reads the out-list of every member of
+ * N+(u) (Section 3.2). The handle may also hold a bit matrix over a set C of
+ * the highest-ranked vertices (every vertex whose ranking key is at least a
+ * threshold, so that an out-neighbour of a vertex of C is in C): bit (a, b)
+ * is set iff C has the arc a -> b. The counting calls then take the row of a
+ * member x of N+(u) from the matrix, one bit per later member of N+(u),
+ * instead of scanning N+(x), where the out-list is the longer of the two
+ * (kc_set_core_policy). Counts are the same with and without it. By default
+ * it is built when the largest out-degree is at least 128 and the builds of
+ * all roots would read, on average, at least 16 out-list entries per arc
+ * (the sum over arcs u -> x of d+(x)), with at most
+ * kc_set_core_policy's max_vertices vertices and a matrix no larger than
+ * the DAG's arrays (64 MiB at least). It costs |C|^2/8 bytes of device memory
+ * and one pass over the keys and the core's arcs.
  */
 kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t stream);
+
+/*
+ * Process-wide settings of the dense core (see kc_orient).
+ *   max_vertices  largest core that kc_orient builds (default 131072 vertices,
+ *                 a 2 GiB matrix); 0: none
+ *   ratio         the counting calls take member x's row from the matrix when
+ *                 d+(x) >= ratio * (members of N+(u) after x) (default 2;
+ *                 0: always, for every member in the core); UINT32_MAX: the
+ *                 counting calls do not use the matrix at all
+ * Read by later kc_orient calls (max_vertices) and later counting calls
+ * (ratio). Not synchronised with calls running on other threads.
+ */
+void kc_set_core_policy(uint32_t max_vertices, uint32_t ratio);
+
+/* Number of vertices in the handle's dense core (0: it has none). */
+uint32_t kc_dag_core_vertices(const kc_dag *d);
 
 /* Release a handle (stream-ordered on the stream it was created on). NULL is a no-op. */
 void kc_dag_free(kc_dag *d);

@@ -17,6 +17,7 @@
 
 #include <atomic>
 
+#include "kc_core.cuh"
 #include "kc_host.cuh"
 
 namespace kc {
@@ -109,6 +110,8 @@ void kc_dag_free(kc_dag *d) {
   if (d->col) cudaFreeAsync(d->col, d->stream);
   if (d->order) cudaFreeAsync(d->order, d->stream);
   if (d->key) cudaFreeAsync(d->key, d->stream);
+  if (d->core_id) cudaFreeAsync(d->core_id, d->stream);
+  if (d->core_bits) cudaFreeAsync(d->core_bits, d->stream);
   delete d;
 }
 
@@ -117,7 +120,9 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   const int base = method & 0xff;
   const int sym = (method & KC_VALIDATE_SYMMETRY) ? 1 : 0;
   if (base != KC_ORIENT_DEGREE && base != KC_ORIENT_GP && base != KC_ORIENT_BE) return KC_EINVAL;
-  if ((method & ~(0xff | KC_VALIDATE_SYMMETRY)) != 0) return KC_EINVAL;
+  if ((method & ~(0xff | KC_VALIDATE_SYMMETRY | KC_CORE_BITS | KC_NO_CORE_BITS)) != 0) return KC_EINVAL;
+  if ((method & KC_CORE_BITS) && (method & KC_NO_CORE_BITS)) return KC_EINVAL;
+  const int core_mode = (method & KC_CORE_BITS) ? kc::kCoreForce : (method & KC_NO_CORE_BITS) ? kc::kCoreOff : kc::kCoreAuto;
   if (g->n > 0 && (!g->d_row_ptr || (g->nnz > 0 && !g->d_col))) return KC_EINVAL;
   if (g->nnz % 2 != 0) return KC_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -204,6 +209,8 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
   auto ge = [&](uint64_t t) -> uint32_t { return t < D->ge.size() ? (uint32_t)D->ge[t] : 0u; };
   KC_CK(kc::launch_sort_rows(D->ptr, D->col, key.as<uint64_t>(), D->order, ge(1025), ge(33), ge(2), maxd, s));
   KC_CK(cudaStreamSynchronize(s));  // `start` is a pageable host buffer read by the copy above
+  const kc_status cst = kc::build_core(D, g->d_row_ptr, key.as<uint64_t>(), core_mode, s);
+  if (cst != KC_OK) return cst;
   D->key = (uint64_t *)key.release();  // kept: peeling compares ranks
   *out = D;
   guard.d = nullptr;
@@ -302,6 +309,13 @@ cudaError_t plan_count(const kc_dag *d, int k_min, bool pv, bool pa, const kc_pa
   a.light_min = (uint32_t)(k_min - 1);
   a.light_max = light;
   a.bulk_build = bulk_build_enabled() ? 1u : 0u;
+  const uint32_t ratio = core_policy().ratio;
+  if (d->core_bits && !a.bulk_build && ratio != 0xffffffffu) {
+    a.core_id = d->core_id;
+    a.core_bits = (const unsigned long long *)d->core_bits;
+    a.core_words = d->core_words;
+    a.core_ratio = ratio;
+  }
   if (a.n_scratch > 0) {
     const size_t slab = (root_layout(d->max_out, pv, pa).bytes + 255) & ~(size_t)255;
     const size_t sbudget = (size_t)4 << 30;

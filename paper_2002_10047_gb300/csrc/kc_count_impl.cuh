@@ -878,6 +878,68 @@ __device__ __forceinline__ void build_rows_bulk(const CountArgs &a, uint32_t d, 
   __syncwarp();
 }
 
+// ------------------------------------------------- dense-core lookups
+// Rows of the induced subgraph read from the dense-core bit matrix (the
+// members involved are all in the core; kc_core.cu). hid[i] is the core
+// number of member i.
+
+// Bits i (rows in m) of column j of the induced subgraph, hj = hid[j]:
+// bit i set iff x_i -> x_j. Four loads in flight per lane.
+__device__ __forceinline__ uint64_t core_column(const CountArgs &a, const uint32_t *hid, uint64_t m, uint32_t hj) {
+  uint64_t c = 0;
+  const unsigned long long *cb = a.core_bits + (hj >> 6);
+  const uint64_t bit = 1ull << (hj & 63);
+  while (m) {
+    int ii[4];
+    uint64_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ii[q] = m ? __ffsll((long long)m) - 1 : -1;
+      m &= m - 1;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] = ii[q] >= 0 ? cb[(size_t)hid[ii[q]] * a.core_words] : 0ull;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (w[q] & bit) c |= 1ull << ii[q];
+  }
+  return c;
+}
+
+// Row i (core number hi) of a block root's induced subgraph: one bit per
+// later member, 128 columns per pass. Other warps may set lower-triangle bits
+// of the same words, hence the atomics.
+template <bool PV>
+__device__ __forceinline__ void core_row(const CountArgs &a, uint64_t *adj, uint32_t W, const uint32_t *hid,
+                                         uint32_t i, uint32_t d, uint32_t hi) {
+  const unsigned lane = lane_id();
+  const unsigned long long *row = a.core_bits + (size_t)hi * a.core_words;
+  for (uint32_t j0 = (i + 1) & ~63u; j0 < d; j0 += 128) {
+    bool h[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t j = j0 + 32 * q + lane;
+      h[q] = false;
+      if (j > i && j < d) {
+        const uint32_t c = hid[j];
+        if (c != kNoCore) h[q] = (row[c >> 6] >> (c & 63)) & 1ull;
+        else atomicOr(a.status, ST_CAPACITY);  // a later member outside the core: cannot happen
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q += 2) {
+      const unsigned lo = __ballot_sync(0xffffffffu, h[q]), up = __ballot_sync(0xffffffffu, h[q + 1]);
+      if (lane == 0 && (lo | up))
+        atomicOr((unsigned long long *)&adj[(size_t)i * W + (j0 >> 6) + q / 2], ((unsigned long long)up << 32) | lo);
+    }
+    if (PV) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (h[q]) atomicOr((unsigned long long *)&adj[(size_t)(j0 + 32 * q + lane) * W + (i >> 6)], 1ull << (i & 63));
+    }
+  }
+}
+
 // ------------------------------------------------------- block-level root
 struct BlockShared {
   unsigned long long red[kRootWarps];
@@ -945,6 +1007,7 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint3
     rl[i] = (uint32_t)(a.ptr[x + 1] - xb);
     if (PV) cnt[i] = 0;
     if (PA) asub[i] = 0;
+    if (a.core_bits) pre[i] = a.core_id[x];  // pre is free until the items are set up
   }
   for (uint32_t s = tid; s < T; s += kRootBlock) tab[s] = kEmptySlot;
   for (size_t w = tid; w < (size_t)d * W; w += kRootBlock) adj[w] = 0;
@@ -988,6 +1051,13 @@ __device__ __forceinline__ void block_root(const CountArgs &a, uint32_t u, uint3
       if (i >= d) break;
       const uint64_t xb = rb[i];
       const uint32_t len = rl[i];
+      if (a.core_bits) {
+        const uint32_t hi = pre[i];
+        if (hi != kNoCore && (uint64_t)len >= (uint64_t)a.core_ratio * (d - 1 - i)) {
+          core_row<PV>(a, adj, W, pre, i, d, hi);
+          continue;
+        }
+      }
       for (uint32_t base = 0; base < len; base += 32 * kBuildUnroll) {
         uint32_t y[kBuildUnroll];
 #pragma unroll
@@ -1236,13 +1306,14 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32
     if (PA) asub[i] = 0;
   }
   for (uint32_t s = lane; s < 128; s += 32) hkey[s] = kEmpty;
-  uint32_t e0 = 0, e1 = 0;
+  uint32_t e0 = 0, e1 = 0, h0 = kNoCore, h1 = kNoCore;
   if (lane < d) {
     const uint32_t x = rc_[b + lane];
     const uint64_t xb = a.ptr[x];
     L[lane] = x;
     rbeg[lane] = xb;
     e0 = (uint32_t)(a.ptr[x + 1] - xb);
+    if (a.core_bits) h0 = a.core_id[x];
   }
   if (lane + 32 < d) {
     const uint32_t x = rc_[b + lane + 32];
@@ -1250,6 +1321,21 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32
     L[lane + 32] = x;
     rbeg[lane + 32] = xb;
     e1 = (uint32_t)(a.ptr[x + 1] - xb);
+    if (a.core_bits) h1 = a.core_id[x];
+  }
+  // rows taken from the dense core (bits ub): members in the core whose
+  // out-list holds at least core_ratio entries per later member; their
+  // out-lists drop out of the scan. pre holds the core numbers until the
+  // items are set up.
+  uint64_t ub = 0;
+  if (a.core_bits) {
+    const bool b0 = h0 != kNoCore && (uint64_t)e0 >= (uint64_t)a.core_ratio * (d - 1 - lane);
+    const bool b1 = h1 != kNoCore && (uint64_t)e1 >= (uint64_t)a.core_ratio * (d - 33 - lane);
+    ub = (uint64_t)__ballot_sync(0xffffffffu, b0) | ((uint64_t)__ballot_sync(0xffffffffu, b1) << 32);
+    if (b0) e0 = 0;
+    if (b1) e1 = 0;
+    pre[lane] = h0;
+    pre[lane + 32] = h1;
   }
   const unsigned z0 = warp_incl_scan(e0), z1 = warp_incl_scan(e1);
   const unsigned tot0 = __shfl_sync(0xffffffffu, z0, 31), tot1 = __shfl_sync(0xffffffffu, z1, 31);
@@ -1287,6 +1373,34 @@ __device__ __forceinline__ void warp_root(const CountArgs &a, uint32_t u, uint32
     }
   }
   __syncwarp();
+  if (ub) {
+    // columns lane and lane + 32 over the rows in ub, then rows by ballot;
+    // lane t owns words t and t + 32 (upper bits from the rows, lower bits,
+    // per vertex only, from the columns)
+    const uint64_t m0 = ub & ((1ull << lane) - 1ull), m1 = ub & ((1ull << (lane + 32)) - 1ull);
+    uint64_t c0 = 0, c1 = 0;
+    if (lane < d && m0) {
+      if (h0 != kNoCore) c0 = core_column(a, pre, m0, h0);
+      else atomicOr(a.status, ST_CAPACITY);  // a later member outside the core: cannot happen
+    }
+    if (lane + 32 < d && m1) {
+      if (h1 != kNoCore) c1 = core_column(a, pre, m1, h1);
+      else atomicOr(a.status, ST_CAPACITY);
+    }
+    uint64_t r0 = 0, r1 = 0;
+    for (uint64_t m = ub; m; m &= m - 1) {
+      const int i = __ffsll((long long)m) - 1;
+      const uint64_t row = (uint64_t)__ballot_sync(0xffffffffu, (c0 >> i) & 1ull) |
+                           ((uint64_t)__ballot_sync(0xffffffffu, (c1 >> i) & 1ull) << 32);
+      if (lane == (unsigned)(i & 31)) {
+        if (i < 32) r0 = row;
+        else r1 = row;
+      }
+    }
+    adj[lane] |= r0 | (PV ? c0 : 0ull);
+    adj[lane + 32] |= r1 | (PV ? c1 : 0ull);
+    __syncwarp();
+  }
   // a root with d <= 64 out-neighbours: an entry counts the root's cliques
   // through one of them, at most C(62, k - 2), below 2^32 for k <= 10
   const bool c32 = k <= 10;

@@ -17,6 +17,7 @@ enum : unsigned {
   ST_STALL = 32u,     // a bulk copy did not complete within its bounded wait
 };
 
+constexpr uint32_t kNoCore = 0xffffffffu;  // core number of a vertex outside the dense core (kc_core.cu)
 constexpr int kBlock = 256;              // threads per block of the orientation kernels
 constexpr int kWarps = kBlock / 32;
 constexpr int kRootBlock = 512;          // threads per block of the block-root counting kernel
@@ -154,6 +155,15 @@ struct CountArgs {
   // the order array writes its total to rooted[rooted_pos[i]]
   unsigned long long *rooted;
   const uint32_t *rooted_pos;
+  // dense core (kc_core.cu; null: none): core_id[v] numbers the core
+  // vertices, core_bits row a (core_words words) has bit b set iff core
+  // vertex a has an arc to core vertex b. A member x_i of N+(u) whose
+  // out-list holds at least core_ratio entries per later member takes its
+  // row of the induced subgraph from core_bits.
+  const uint32_t *core_id;
+  const unsigned long long *core_bits;
+  uint32_t core_words;
+  uint32_t core_ratio;
 };
 
 // A configured counting pass (kc_api.cu).

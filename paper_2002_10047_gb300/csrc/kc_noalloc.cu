@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "kc_core.cuh"
 #include "kc_dag.cuh"
 #include "kc_host.cuh"
 #include "kc_internal.cuh"
@@ -107,6 +108,13 @@ extern "C" kc_status kc_count_noalloc(const kc_dag *d, int k, uint64_t *h_total,
   a.n_big = ge(kc::kLightMax + 1);
   a.n_scratch = ge((uint64_t)dcap + 1);
   a.bulk_build = kc::bulk_build_enabled() ? 1u : 0u;
+  const uint32_t ratio = kc::core_policy().ratio;
+  if (d->core_bits && !a.bulk_build && ratio != 0xffffffffu) {  // the dense core is the DAG's own
+    a.core_id = d->core_id;
+    a.core_bits = (const unsigned long long *)d->core_bits;
+    a.core_words = d->core_words;
+    a.core_ratio = ratio;
+  }
   uint8_t *b = (uint8_t *)base;
   a.total = (unsigned long long *)b;
   a.status = (unsigned *)(b + 8);

@@ -321,6 +321,12 @@ kc_status peel_run(const kc_csr *g, const kc_dag *d, int k, bool approx, uint64_
         rows.ptr = d->ptr;
         rows.col = d->col;
         rows.order = rorder.as<uint32_t>();
+        // candidate rows are subsets of out-lists, sorted by rank: the DAG's
+        // dense core serves their builds as it serves the out-lists'
+        rows.core_id = d->core_id;
+        rows.core_bits = d->core_bits;
+        rows.core_words = d->core_words;
+        rows.core_n = d->core_n;
         rows.ge.assign((size_t)h_maxlen + 2, 0);
         for (int64_t t = h_maxlen; t >= 0; --t) rows.ge[t] = rows.ge[t + 1] + h_hist[t];
         // `start` outlives the copy: it is rewritten only after the next

@@ -26,6 +26,8 @@ KC_ORIENT_DEGREE = 0
 KC_ORIENT_GP = 1
 KC_ORIENT_BE = 2
 KC_VALIDATE_SYMMETRY = 0x100
+KC_CORE_BITS = 0x200
+KC_NO_CORE_BITS = 0x400
 KC_LIGHT_BY_DEGREE = 1
 KC_LIGHT_BY_ID = 2
 _METHODS = {"degree": KC_ORIENT_DEGREE, "gp": KC_ORIENT_GP, "be": KC_ORIENT_BE}
@@ -150,6 +152,10 @@ def _load():
         lib.kc_measure_word_op_rate.restype = I
         lib.kc_set_bulk_build.argtypes = [ctypes.c_int]
         lib.kc_set_bulk_build.restype = None
+        lib.kc_set_core_policy.argtypes = [U32, U32]
+        lib.kc_set_core_policy.restype = None
+        lib.kc_dag_core_vertices.argtypes = [P]
+        lib.kc_dag_core_vertices.restype = U32
         lib.kc_debug_fail_allocations_after.argtypes = [ctypes.c_int64]
         lib.kc_debug_fail_allocations_after.restype = None
         lib.kc_kernel_launches.argtypes = []
@@ -215,6 +221,11 @@ class Dag:
     def max_out_degree(self) -> int:
         return int(_load().kc_dag_max_out_degree(self._h))
 
+    @property
+    def core_vertices(self) -> int:
+        """Vertices in the dense core (0: the handle has none)."""
+        return int(_load().kc_dag_core_vertices(self._h))
+
     def export(self, stream=None):
         """(ptr int64[n+1], col int32[m]) device tensors of the out-lists."""
         ptr = torch.empty(self.n + 1, dtype=torch.int64, device=self.device)
@@ -235,8 +246,10 @@ class Dag:
 
 
 def kc_orient(row_ptr: torch.Tensor, col: torch.Tensor, n: int | None = None, method: str = "degree",
-              validate_symmetry: bool = False, stream=None) -> Dag:
-    """Orient(G): rank and direct a simple undirected CSR held in device memory."""
+              validate_symmetry: bool = False, stream=None, core: bool | None = None) -> Dag:
+    """Orient(G): rank and direct a simple undirected CSR held in device memory.
+    core: build the dense-core bit matrix always (True), never (False) or where
+    it pays (None)."""
     _require_cuda(row_ptr, "row_ptr", (torch.int64,))
     _require_cuda(col, "col", (torch.int32,))
     n = row_ptr.numel() - 1 if n is None else n
@@ -244,6 +257,8 @@ def kc_orient(row_ptr: torch.Tensor, col: torch.Tensor, n: int | None = None, me
         raise ValueError("row_ptr must have n+1 entries")
     g = _Csr(n, col.numel(), row_ptr.data_ptr(), col.data_ptr() if col.numel() else 0)
     flags = _METHODS[method] | (KC_VALIDATE_SYMMETRY if validate_symmetry else 0)
+    if core is not None:
+        flags |= KC_CORE_BITS if core else KC_NO_CORE_BITS
     h = ctypes.c_void_p()
     _check(_load().kc_orient(ctypes.byref(g), flags, ctypes.byref(h), _stream(stream)))
     return Dag(h.value, row_ptr.device)
@@ -527,6 +542,14 @@ def kc_set_bulk_build(enabled: bool):
     """Block-root builds stage the members' out-lists with bulk copies (True) or read them
     with ordinary loads (False, the default); counts are identical."""
     _load().kc_set_bulk_build(1 if enabled else 0)
+
+
+def kc_set_core_policy(max_vertices: int = 131072, ratio: int = 2):
+    """Dense core: largest core later orientations build (0: none), and the
+    lookup rule of later counts (a member's row comes from the core when its
+    out-degree is at least ratio times the members after it; 0: always;
+    2**32 - 1: never). Counts are identical either way."""
+    _load().kc_set_core_policy(int(max_vertices), int(ratio))
 
 
 def kc_debug_fail_allocations_after(count: int):

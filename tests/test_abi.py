@@ -88,10 +88,31 @@ def test_binding_constants_match_the_header():
     text = open(os.path.join(ROOT, "include", "kclique.h")).read()
     defines = {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define (KC_\w+) (0x[0-9a-fA-F]+|\d+)\b", text)}
     for name in ("KC_KMAX", "KC_ORIENT_DEGREE", "KC_ORIENT_GP", "KC_ORIENT_BE", "KC_VALIDATE_SYMMETRY",
-                 "KC_LIGHT_BY_DEGREE", "KC_LIGHT_BY_ID"):
+                 "KC_CORE_BITS", "KC_NO_CORE_BITS", "KC_LIGHT_BY_DEGREE", "KC_LIGHT_BY_ID"):
         assert getattr(kc, name) == defines[name], name
     enum = dict((m.group(1), int(m.group(2))) for m in re.finditer(r"(KC_E?\w+) = (\d+)", text))
     for name in ("KC_OK", "KC_EINVAL", "KC_ERANGE", "KC_ENOMEM", "KC_ETIMEDOUT", "KC_ECUDA", "KC_ECAPACITY"):
         assert getattr(kc, name) == enum[name], name
     assert kc._METHODS == {"degree": defines["KC_ORIENT_DEGREE"], "gp": defines["KC_ORIENT_GP"],
                            "be": defines["KC_ORIENT_BE"]}
+
+
+def test_orient_rejects_bad_flags_without_gpu(lib_path):
+    """kc_orient checks its method flags before any device call: unknown bits
+    and KC_CORE_BITS together with KC_NO_CORE_BITS give KC_EINVAL."""
+    lib = ctypes.CDLL(lib_path)
+    lib.kc_kernel_launches.restype = ctypes.c_uint64
+
+    class Csr(ctypes.Structure):
+        _fields_ = [("n", ctypes.c_uint32), ("nnz", ctypes.c_uint64), ("rp", ctypes.c_void_p),
+                    ("col", ctypes.c_void_p)]
+
+    g = Csr(0, 0, None, None)
+    h = ctypes.c_void_p()
+    before = lib.kc_kernel_launches()
+    assert lib.kc_orient(ctypes.byref(g), 0x200 | 0x400, ctypes.byref(h), None) == 1
+    assert lib.kc_orient(ctypes.byref(g), 0x800, ctypes.byref(h), None) == 1
+    assert lib.kc_orient(ctypes.byref(g), 3, ctypes.byref(h), None) == 1
+    assert h.value is None
+    assert lib.kc_kernel_launches() == before
+

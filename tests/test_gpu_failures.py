@@ -67,6 +67,7 @@ def test_injected_allocation_failures(kc):
     calls = {
         "orient": lambda: kc.orient(rp, col, g.n).free(),
         "orient_gp": lambda: kc.orient(rp, col, g.n, method="gp").free(),
+        "orient_core": lambda: kc.orient(rp, col, g.n, core=True).free(),
         "count": lambda: kc.count(dag, 4),
         "count_per_vertex": lambda: kc.count_per_vertex(dag, 4),
         "count_roots": lambda: kc.count_roots(dag, 4, torch.arange(100, dtype=torch.int32, device="cuda")),
@@ -74,7 +75,7 @@ def test_injected_allocation_failures(kc):
     }
     for name, call in calls.items():
         failed = 0
-        for after in range(0, 12):
+        for after in range(0, 16):
             kc.kc_debug_fail_allocations_after(after)
             try:
                 call()
