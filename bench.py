@@ -84,6 +84,18 @@ def parse():
     return ap.parse_args()
 
 
+def build_bytes(n: int, m: int, st: dict) -> int:
+    """Algorithmic bytes of one counting pass (first-level induced subgraphs,
+    Section 3.4): root offsets + root list + out-neighbour offsets + out-lists
+    of the roots + the out-list entries the builds scan, and, where the DAG
+    has a dense core, the members' core numbers and one 64-bit word per core
+    bit looked up instead of a scan."""
+    b = 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * st["build_scanned"] + 8 * st["build_lookups"]
+    if st.get("core_vertices"):
+        b += 4 * m
+    return b
+
+
 def max_over_ranks(t: float, world: int, device) -> float:
     """The slowest rank's step time (every rank gets it)."""
     if world <= 1:
@@ -610,9 +622,8 @@ def run_ours(args, rank, world):
     st = kc.dag_stats(dag)
     m = dag.m
     dag.free()
-    # algorithmic bytes of one counting pass (first-level induced subgraphs, Section 3.4):
-    # root offsets + root list + out-neighbour offsets + out-neighbour lists + per-vertex output
-    b_count = 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * st["sum_arc_head"] + 8 * n
+    # algorithmic bytes of one counting pass plus the per-vertex output
+    b_count = build_bytes(n, m, st) + 8 * n
     # algorithmic integer work of one pass: one bitset intersect (64-bit AND +
     # popcount) per j-clique prefix below the root, j = 3 .. k-1 (Algorithm 1)
     cliques = {3: st["triangles"]}
@@ -667,6 +678,7 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "ks": ks, "n": n, "m": m, "orientation": "degree",
+                   "dense_core_vertices": st["core_vertices"],
                    "l2": "flushed between steps (512 MiB write, outside step events)",
                    "parallelism": f"replicas x{world}"},
         "per_k": per_k, "orient_ms": sum(orient_ms) / len(orient_ms),
@@ -955,7 +967,7 @@ def run_batch(args, rank, world):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     st = kc.dag_stats(dag)
     n, m = u.n, dag.m
-    b_count = 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * st["sum_arc_head"] + 8 * G + 8 * (G + 1) + G
+    b_count = build_bytes(n, m, st) + 8 * G + 8 * (G + 1) + G
     achieved = b_count / (t_step / 1e3) / 1e9
     line = {
         "metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": world, "steps": args.steps,
@@ -1319,7 +1331,7 @@ def chunglu_summary(args, kc, dev):
     t4, ms_c = timed(lambda: kc.count(dag, 4))
     (t4b, _), ms_pv = timed(lambda: kc.count_per_vertex(dag, 4, out=pv))
     st = kc.dag_stats(dag)
-    b_count = 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * st["sum_arc_head"]
+    b_count = build_bytes(n, m, st)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1328,7 +1340,10 @@ def chunglu_summary(args, kc, dev):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     ach = b_count / (ms_c / 1e3) / 1e9
-    out.update({"m": m, "max_out_degree": st["max_out"], "k4": {
+    out.update({"m": m, "max_out_degree": st["max_out"],
+                "dense_core": {"vertices": st["core_vertices"], "build_scanned": st["build_scanned"],
+                               "build_lookups": st["build_lookups"], "plain_build_volume": st["sum_arc_head"]},
+                "k4": {
         "cliques": t4, "count_ms": ms_c, "per_vertex_ms": ms_pv, "cliques_per_s": t4 / (ms_c / 1e3),
         "roofline": {"bound": "hbm", "kernel": "count_block_kernel + count_warp_kernel, total, k=4",
                      "achieved": ach, "peak": hbm_peak,
@@ -1512,7 +1527,7 @@ def run_chunglu(args, rank, world):
     st = kc.dag_stats(dag)
     m = dag.m
     dag.free()
-    b_count = 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * st["sum_arc_head"]
+    b_count = build_bytes(n, m, st)
     achieved = b_count / (t_count / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

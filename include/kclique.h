@@ -119,7 +119,7 @@ kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t strea
  *   max_vertices  largest core that kc_orient builds (default 131072 vertices,
  *                 a 2 GiB matrix); 0: none
  *   ratio         the counting calls take member x's row from the matrix when
- *                 d+(x) >= ratio * (members of N+(u) after x) (default 2;
+ *                 d+(x) >= ratio * (members of N+(u) after x) (default 1;
  *                 0: always, for every member in the core); UINT32_MAX: the
  *                 counting calls do not use the matrix at all
  * Read by later kc_orient calls (max_vertices) and later counting calls
@@ -484,12 +484,21 @@ kc_status kc_peel_approx(const kc_csr *g, const kc_dag *d, int k, uint32_t eps_n
  *                  first-level induced subgraphs of Section 3.4)
  *   triangles      number of 3-cliques
  *   max_out        largest out-degree
+ *   core_vertices  vertices in the dense core (kc_orient), 0 if none
+ *   build_scanned  out-list entries those builds scan under the current
+ *                  dense-core rule (kc_set_core_policy); sum_arc_head without
+ *                  a core
+ *   build_lookups  dense-core bits they look up instead (one 64-bit word read
+ *                  each); 0 without a core
  */
 typedef struct {
   uint64_t sum_out_sq;
   uint64_t sum_arc_head;
   uint64_t triangles;
   uint32_t max_out;
+  uint32_t core_vertices;
+  uint64_t build_scanned;
+  uint64_t build_lookups;
 } kc_dag_stats;
 kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t stream);
 

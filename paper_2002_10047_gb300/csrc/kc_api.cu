@@ -59,6 +59,11 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
+kc_status internal_fail(const char *what) {
+  g_cuda_err = what;
+  return KC_ECUDA;
+}
+
 kc_status status_code(unsigned st) {
   if (st & ST_STALL) {
     g_cuda_err = "a bulk copy of the counting kernels did not complete";
@@ -239,10 +244,16 @@ kc_status kc_dag_get_stats(const kc_dag *d, kc_dag_stats *h_stats, kc_stream_t s
   uint64_t tri = 0;
   const kc_status st = kc::run_count(d, 3, nullptr, nullptr, &tri, 0, s);
   if (st != KC_OK) return st;
+  uint64_t scanned = 0, looked = 0;
+  const kc_status st2 = kc::core_build_split(d, &scanned, &looked, s);
+  if (st2 != KC_OK) return st2;
   h_stats->sum_out_sq = h[0];
   h_stats->sum_arc_head = h[1];
   h_stats->triangles = tri;
   h_stats->max_out = d->max_out;
+  h_stats->core_vertices = d->core_n;
+  h_stats->build_scanned = scanned;
+  h_stats->build_lookups = looked;
   return KC_OK;
 }
 

@@ -33,12 +33,13 @@ constexpr int kCoreBlock = 512;
 
 __device__ __forceinline__ unsigned lane_of() { return threadIdx.x & 31u; }
 
-// Histogram of one 11-bit digit of the keys whose bits above the digit equal
-// `prefix` (all keys when match_shift >= 64). Lanes with equal digits add
-// once per group.
+// Histogram of one digit (bits shift .. match_shift-1, at most 11) of the keys
+// whose bits from match_shift up equal `prefix` (all keys when match_shift
+// >= 64). Lanes with equal digits add once per group.
 __global__ void __launch_bounds__(kCoreBlock) key_digit_hist_kernel(const uint64_t *__restrict__ key, uint32_t n,
                                                                     int shift, int match_shift, uint64_t prefix,
                                                                     unsigned *hist) {
+  const uint32_t dmask = (1u << (match_shift - shift)) - 1u;
   __shared__ unsigned h[kBins];
   for (uint32_t b = threadIdx.x; b < kBins; b += blockDim.x) h[b] = 0;
   __syncthreads();
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(kCoreBlock) key_digit_hist_kernel(const uint64
     if (v < n) {
       const uint64_t k = key[v];
       ok = match_shift >= 64 || (k >> match_shift) == prefix;
-      dig = (uint32_t)(k >> shift) & (kBins - 1u);
+      dig = (uint32_t)(k >> shift) & dmask;
     }
     const unsigned act = __ballot_sync(0xffffffffu, ok);
     if (ok) {
@@ -121,9 +122,61 @@ __global__ void __launch_bounds__(kCoreBlock) build_volume_kernel(const uint64_t
 }
 
 std::atomic<uint32_t> g_core_max{131072};
-std::atomic<uint32_t> g_core_ratio{2};
+std::atomic<uint32_t> g_core_ratio{1};
+
+// Out-list entries scanned and core bits looked up by the level-2 builds of
+// all roots under the counting kernels' rule (acc[0], acc[1]): one warp per
+// root, lanes over its members.
+__global__ void __launch_bounds__(kCoreBlock) core_build_split_kernel(const uint64_t *__restrict__ ptr,
+                                                                      const uint32_t *__restrict__ col, uint32_t n,
+                                                                      const uint32_t *__restrict__ core_id,
+                                                                      uint32_t ratio, unsigned long long *acc) {
+  const size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long scanned = 0, looked = 0;
+  for (size_t u = warp; u < n; u += nwarps) {
+    const uint64_t b = ptr[u];
+    const uint32_t d = (uint32_t)(ptr[u + 1] - b);
+    for (uint32_t i = lane_of(); i < d; i += 32) {
+      const uint32_t x = col[b + i];
+      const uint64_t len = ptr[x + 1] - ptr[x];
+      const uint32_t later = d - 1 - i;
+      if (core_id && core_id[x] != kNoCore && len >= (uint64_t)ratio * later) looked += later;
+      else scanned += len;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    scanned += __shfl_xor_sync(0xffffffffu, scanned, o);
+    looked += __shfl_xor_sync(0xffffffffu, looked, o);
+  }
+  if (lane_of() == 0) {
+    if (scanned) atomicAdd(&acc[0], scanned);
+    if (looked) atomicAdd(&acc[1], looked);
+  }
+}
 
 }  // namespace
+
+kc_status core_build_split(const kc_dag *D, uint64_t *scanned, uint64_t *looked, cudaStream_t s) {
+  *scanned = *looked = 0;
+  if (D->n == 0 || D->m == 0) return KC_OK;
+  const uint32_t ratio = core_policy().ratio;
+  const bool use = D->core_bits && ratio != 0xffffffffu;
+  DevBuf acc;
+  KC_CK(acc.alloc(sizeof(unsigned long long) * 2, s));
+  KC_CK(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * 2, s));
+  core_build_split_kernel<<<(unsigned)sm_count() * 8, kCoreBlock, 0, s>>>(
+      D->ptr, D->col, D->n, use ? D->core_id : nullptr, ratio, acc.as<unsigned long long>());
+  note_launch();
+  KC_CK(cudaGetLastError());
+  unsigned long long h[2];
+  KC_CK(cudaMemcpyAsync(h, acc.p, sizeof h, cudaMemcpyDeviceToHost, s));
+  KC_CK(cudaStreamSynchronize(s));
+  *scanned = h[0];
+  *looked = h[1];
+  return KC_OK;
+}
 
 CorePolicy core_policy() {
   CorePolicy p;
@@ -191,7 +244,7 @@ kc_status build_core(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mod
         if (cum + h[b] >= r) break;
         cum += h[b];
       }
-      if (b < 0) return KC_ECUDA;  // the digit counts do not add up: cannot happen
+      if (b < 0) return internal_fail("dense core: key digit counts do not add up");
       r -= cum;
       prefix = (prefix << width) | (uint64_t)b;
     }
@@ -210,7 +263,7 @@ kc_status build_core(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mod
   if (H == 0 || H > hmax) {  // no core (kappa above every key), or a miscount
     cudaFreeAsync(D->core_id, s);
     D->core_id = nullptr;
-    return H == 0 ? KC_OK : KC_ECUDA;
+    return H == 0 ? KC_OK : internal_fail("dense core: more vertices above the threshold than selected");
   }
   const uint32_t words = (H + 63u) / 64u;
   const size_t bytes = (size_t)H * words * 8;
@@ -223,7 +276,7 @@ kc_status build_core(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mod
   unsigned st = 0;
   KC_CK(cudaMemcpyAsync(&st, ctr.as<unsigned>() + 1, sizeof st, cudaMemcpyDeviceToHost, s));
   KC_CK(cudaStreamSynchronize(s));
-  if (st) return KC_ECUDA;
+  if (st) return internal_fail("dense core: an out-neighbour of a core vertex is outside the core");
   D->core_n = H;
   D->core_words = words;
   return KC_OK;

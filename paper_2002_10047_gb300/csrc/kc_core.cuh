@@ -24,4 +24,9 @@ CorePolicy core_policy();
 // max_vertices); kCoreOff never.
 kc_status build_core(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mode, cudaStream_t s);
 
+// Out-list entries scanned and core bits looked up by the level-2 builds of
+// all roots of D under the current lookup rule (no core: scanned = sum over
+// arcs u->x of d+(x), looked = 0).
+kc_status core_build_split(const kc_dag *D, uint64_t *scanned, uint64_t *looked, cudaStream_t s);
+
 }  // namespace kc

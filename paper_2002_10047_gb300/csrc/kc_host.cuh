@@ -12,6 +12,9 @@ namespace kc {
 
 // Records the CUDA error text for kc_last_cuda_error and maps it to a status.
 kc_status cuda_fail(cudaError_t e);
+// An internal consistency check failed: records `what` for
+// kc_last_cuda_error and returns KC_ECUDA.
+kc_status internal_fail(const char *what);
 // Device status word (ST_* bits) to the kc_status the caller sees.
 kc_status status_code(unsigned st);
 int sm_count();

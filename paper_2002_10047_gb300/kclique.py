@@ -83,7 +83,9 @@ class _PeelResult(ctypes.Structure):
 
 class _Stats(ctypes.Structure):
     _fields_ = [("sum_out_sq", ctypes.c_uint64), ("sum_arc_head", ctypes.c_uint64),
-                ("triangles", ctypes.c_uint64), ("max_out", ctypes.c_uint32)]
+                ("triangles", ctypes.c_uint64), ("max_out", ctypes.c_uint32),
+                ("core_vertices", ctypes.c_uint32), ("build_scanned", ctypes.c_uint64),
+                ("build_lookups", ctypes.c_uint64)]
 
 
 _lock = threading.Lock()
@@ -518,7 +520,9 @@ def kc_dag_get_stats(dag: Dag, stream=None) -> dict:
     st = _Stats()
     _check(_load().kc_dag_get_stats(dag.handle, ctypes.byref(st), _stream(stream)))
     return {"sum_out_sq": int(st.sum_out_sq), "sum_arc_head": int(st.sum_arc_head),
-            "triangles": int(st.triangles), "max_out": int(st.max_out)}
+            "triangles": int(st.triangles), "max_out": int(st.max_out),
+            "core_vertices": int(st.core_vertices), "build_scanned": int(st.build_scanned),
+            "build_lookups": int(st.build_lookups)}
 
 
 def kc_checked_sum(values: torch.Tensor, stream=None) -> int:
@@ -544,7 +548,7 @@ def kc_set_bulk_build(enabled: bool):
     _load().kc_set_bulk_build(1 if enabled else 0)
 
 
-def kc_set_core_policy(max_vertices: int = 131072, ratio: int = 2):
+def kc_set_core_policy(max_vertices: int = 131072, ratio: int = 1):
     """Dense core: largest core later orientations build (0: none), and the
     lookup rule of later counts (a member's row comes from the core when its
     out-degree is at least ratio times the members after it; 0: always;

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-DEFAULT = (131072, 2)
+DEFAULT = (131072, 1)
 
 
 @pytest.fixture(scope="module")
@@ -72,9 +72,10 @@ def want(graphs):
 
 
 def policies(n):
-    """(max_vertices, ratio): every vertex in the core, an eighth of them, the
-    default rule, and the lookup path for every member in the core."""
-    return [(n, 0), (max(64, n // 8), 0), DEFAULT, (max(64, n // 8), 1)]
+    """(max_vertices, ratio): every vertex in the core and every member in it
+    looked up, an eighth of them looked up, the default rule, and a rule that
+    mixes lookups and scans inside one root (ratio 4)."""
+    return [(n, 0), (max(64, n // 8), 0), DEFAULT, (max(64, n // 8), 4)]
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
@@ -139,6 +140,13 @@ def test_core_switches(kc, graphs, want):
     assert st["max_out"] >= 128 and st["sum_arc_head"] >= 16 * plain.m
     dag = kc.orient(rp, col, g.n)
     assert dag.core_vertices > 0
+    # the build split under the default rule: fewer out-list entries scanned
+    # than the plain build volume, and some rows looked up instead
+    sc = kc.dag_stats(dag)
+    assert sc["core_vertices"] == dag.core_vertices
+    assert st["core_vertices"] == 0 and st["build_lookups"] == 0 and st["build_scanned"] == st["sum_arc_head"]
+    assert sc["sum_arc_head"] == st["sum_arc_head"] and 0 < sc["build_scanned"] < st["sum_arc_head"]
+    assert sc["build_lookups"] > 0
     ge = graphs["er2000"]
     rpe, cole = kc.csr_to_device(ge)
     assert kc.orient(rpe, cole, ge.n).core_vertices == 0
@@ -149,7 +157,7 @@ def test_core_switches(kc, graphs, want):
     finally:
         kc.kc_set_core_policy(*DEFAULT)
     assert kc.count(dag, 4) == per_k[4][0]
-    kc.kc_set_core_policy(0, 2)  # no core at all
+    kc.kc_set_core_policy(0, 1)  # no core at all
     try:
         assert kc.orient(rp, col, g.n, core=True).core_vertices == 0
     finally:
@@ -166,6 +174,10 @@ def test_core_complete_graphs(kc, n, ks):
     try:
         dag = kc.orient(rp, col, g.n, core=True)
         assert dag.core_vertices == n
+        st = kc.dag_stats(dag)
+        # every member looked up: one bit per pair of N+(u), sum over u of
+        # C(d+(u), 2) = C(n, 3), and nothing scanned
+        assert st["build_scanned"] == 0 and st["build_lookups"] == math.comb(n, 3)
         for k in ks:
             assert kc.count(dag, k) == math.comb(n, k)
             tot, pv = kc.count_per_vertex(dag, k)
@@ -192,3 +204,35 @@ def test_core_peel(kc, graphs):
                 (w.best_cliques, w.best_vertices, w.best_rounds), k
     finally:
         kc.kc_set_core_policy(*DEFAULT)
+
+
+def test_core_threshold_digits(kc, graphs, want):
+    """The core threshold is found digit by digit over the 64-bit keys: a
+    boundary key above 2^9 (degrees 519 / 599 / 699, the core being the K_700
+    whose 700 vertices outrank the rest) and Goodrich-Pszona keys (round in
+    the high word) give the same counts."""
+    g = gg.disjoint_union([gg.complete(520), gg.complete(600), gg.complete(700)])
+    rp, col = kc.csr_to_device(g)
+    kc.kc_set_core_policy(800, 0)
+    try:
+        dag = kc.orient(rp, col, g.n, core=True)
+        assert dag.core_vertices == 700
+        for k in (3, 4):
+            want_k = math.comb(520, k) + math.comb(600, k) + math.comb(700, k)
+            assert kc.count(dag, k) == want_k
+            tot, pv = kc.count_per_vertex(dag, k)
+            assert tot == want_k
+        for name in ("rmat12", "planted", "chung_lu_40k"):
+            h = graphs[name]
+            od, per_k = want[name]
+            rph, colh = kc.csr_to_device(h)
+            kc.kc_set_core_policy(max(64, h.n // 8), 0)
+            dag = kc.orient(rph, colh, h.n, method="gp", core=True)
+            assert dag.core_vertices > 0, name
+            for k in (3, 4):
+                tot, pv = kc.count_per_vertex(dag, k)
+                assert tot == per_k[k][0], (name, k)
+                np.testing.assert_array_equal(kc.as_uint64(pv), per_k[k][1], err_msg=f"{name} gp k={k}")
+    finally:
+        kc.kc_set_core_policy(*DEFAULT)
+
