@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kBlock) count_out_kernel(const uint64_t *__res
   const size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
   const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
   const unsigned lane = lane_id();
+  unsigned cmax = 0;  // one atomic per warp: a per-row atomic on one word serialises
   for (size_t u = warp; u < n; u += nwarps) {
     const uint64_t ku = key[u];
     unsigned c = 0;
@@ -86,11 +87,10 @@ __global__ void __launch_bounds__(kBlock) count_out_kernel(const uint64_t *__res
       c += ranks_below(ku, (uint32_t)u, key[v], v);
     }
     c = warp_sum(c);
-    if (lane == 0) {
-      outdeg[u] = c;
-      atomicMax(maxdeg, c);
-    }
+    if (lane == 0) outdeg[u] = c;
+    cmax = c > cmax ? c : cmax;
   }
+  if (lane == 0 && cmax) atomicMax(maxdeg, cmax);
 }
 
 __global__ void __launch_bounds__(kBlock) write_out_kernel(const uint64_t *__restrict__ rp,
@@ -213,20 +213,39 @@ cudaError_t exclusive_scan_u32(const uint32_t *in, uint64_t *out, size_t n, uint
 }
 
 // ---------------------------------------------------- root work ordering
+// Most vertices share a few small out-degrees, so lanes with equal
+// out-degrees add once per group (one atomic per distinct value in a warp).
 __global__ void outdeg_hist_kernel(const uint64_t *__restrict__ dp, uint32_t n, unsigned *hist, uint32_t maxd) {
-  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
-    const uint64_t d = dp[v + 1] - dp[v];
-    if (d <= maxd) atomicAdd(&hist[d], 1u);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t base = (size_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const size_t v = base + threadIdx.x;
+    const uint64_t d = v < n ? dp[v + 1] - dp[v] : ~0ull;
+    const bool ok = d <= maxd;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const unsigned grp = __match_any_sync(act, (unsigned)d);
+      if (lane_id() == (unsigned)(__ffs(grp) - 1)) atomicAdd(&hist[d], (unsigned)__popc(grp));
+    }
   }
 }
 
-// cursor[d] starts at the first slot of out-degree d in descending order
+// cursor[d] starts at the first slot of out-degree d in descending order; a
+// group of lanes with equal out-degree reserves its slots with one atomic
 __global__ void outdeg_scatter_kernel(const uint64_t *__restrict__ dp, uint32_t n, unsigned *cursor,
                                       uint32_t maxd, uint32_t *__restrict__ order) {
-  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
-    const uint64_t d = dp[v + 1] - dp[v];
-    if (d <= maxd) {
-      const unsigned at = atomicAdd(&cursor[d], 1u);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const unsigned lane = lane_id();
+  for (size_t base = (size_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const size_t v = base + threadIdx.x;
+    const uint64_t d = v < n ? dp[v + 1] - dp[v] : ~0ull;
+    const bool ok = d <= maxd;
+    const unsigned act = __ballot_sync(0xffffffffu, ok);
+    if (ok) {
+      const unsigned grp = __match_any_sync(act, (unsigned)d);
+      const int leader = __ffs(grp) - 1;
+      unsigned at = 0;
+      if (lane == (unsigned)leader) at = atomicAdd(&cursor[d], (unsigned)__popc(grp));
+      at = __shfl_sync(grp, at, leader) + (unsigned)__popc(grp & ((1u << lane) - 1u));
       if (at < n) order[at] = (uint32_t)v;
     }
   }
