@@ -109,8 +109,10 @@ typedef struct kc_dag kc_dag;
  * all roots would read, on average, at least 16 out-list entries per arc
  * (the sum over arcs u -> x of d+(x)), with at most
  * kc_set_core_policy's max_vertices vertices and a matrix no larger than
- * the DAG's arrays (64 MiB at least). It costs |C|^2/8 bytes of device memory
- * and one pass over the keys and the core's arcs.
+ * the DAG's arrays (64 MiB at least) and no larger than a quarter of the free
+ * device memory; if its allocation fails the handle simply has no core.
+ * It costs |C|^2/8 bytes of device memory and one pass over the keys and the
+ * core's arcs. With KC_CORE_BITS a failed allocation gives KC_ENOMEM.
  */
 kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t stream);
 

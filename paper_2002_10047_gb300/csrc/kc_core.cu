@@ -187,7 +187,9 @@ CorePolicy core_policy() {
   return p;
 }
 
-kc_status build_core(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mode, cudaStream_t s) {
+namespace {
+
+kc_status build_core_impl(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mode, cudaStream_t s) {
   const uint32_t n = D->n;
   const CorePolicy pol = core_policy();
   if (mode == kCoreOff || pol.max_vertices == 0 || n == 0 || D->m == 0) return KC_OK;
@@ -215,6 +217,14 @@ kc_status build_core(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mod
     const double cap_bits = 8.0 * std::max(dag_bytes, 64.0 * 1024 * 1024);
     const uint64_t by_mem = (uint64_t)std::sqrt(cap_bits);
     hmax = std::min<uint64_t>(hmax, by_mem & ~(uint64_t)63);
+    // and at most a quarter of the device memory free now
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const uint64_t by_free = (uint64_t)std::sqrt(8.0 * (double)free_b / 4.0);
+      hmax = std::min<uint64_t>(hmax, by_free & ~(uint64_t)63);
+    } else {
+      cudaGetLastError();
+    }
   }
   hmax = std::min<uint64_t>(hmax, n);
   if (hmax < 64 && mode != kCoreForce) return KC_OK;
@@ -280,6 +290,22 @@ kc_status build_core(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mod
   D->core_n = H;
   D->core_words = words;
   return KC_OK;
+}
+
+}  // namespace
+
+kc_status build_core(kc_dag *D, const uint64_t *rp, const uint64_t *key, int mode, cudaStream_t s) {
+  const kc_status st = build_core_impl(D, rp, key, mode, s);
+  if (st == KC_ENOMEM && mode == kCoreAuto) {
+    // the core is optional: without memory for it the handle has none
+    if (D->core_id) cudaFreeAsync(D->core_id, s);
+    if (D->core_bits) cudaFreeAsync(D->core_bits, s);
+    D->core_id = nullptr;
+    D->core_bits = nullptr;
+    D->core_n = D->core_words = 0;
+    return KC_OK;
+  }
+  return st;
 }
 
 }  // namespace kc

@@ -91,3 +91,33 @@ def test_injected_allocation_failures(kc):
     tot, pv = kc.count_per_vertex(dag, 4)
     assert tot == want4
     np.testing.assert_array_equal(kc.as_uint64(pv), want4_pv)
+
+
+def test_automatic_core_is_optional_under_allocation_failure(kc):
+    """The dense core that kc_orient builds by default (here: R-MAT 14, largest
+    out-degree 144) is optional: when one of its allocations fails the handle
+    comes back without a core and counts the same; failures before it still
+    give KC_ENOMEM, and nothing stays allocated either way."""
+    g = gg.rmat(14, 16, seed=5)
+    rp, col = kc.csr_to_device(g)
+    want = oracle.count(oracle.orient(g, "degree"), 4, threads=8)
+    full = kc.orient(rp, col, g.n)
+    assert full.core_vertices > 0
+    full.free()
+    base = pool_used()
+    coreless = 0
+    for after in range(0, 24):
+        kc.kc_debug_fail_allocations_after(after)
+        try:
+            dag = kc.orient(rp, col, g.n)
+        except kc.KcError as e:
+            assert e.status == kc.KC_ENOMEM, (after, e.status)
+            dag = None
+        finally:
+            kc.kc_debug_fail_allocations_after(-1)
+        if dag is not None:
+            coreless += dag.core_vertices == 0
+            assert kc.count(dag, 4) == want, after
+            dag.free()
+        assert pool_used() == base, after
+    assert coreless >= 1
