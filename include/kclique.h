@@ -96,23 +96,24 @@ typedef struct kc_dag kc_dag;
  * row_ptr consistent; symmetry on request): a violation gives KC_EINVAL.
  * Synchronises `stream`. Free the handle with kc_dag_free.
  *
- * Dense core (a layout of the DAG; the paper has no counterpart). The
- * induced-subgraph build of a root u reads the out-list of every member of
- * N+(u) (Section 3.2). The handle may also hold a bit matrix over a set C of
- * the highest-ranked vertices (every vertex whose ranking key is at least a
- * threshold, so that an out-neighbour of a vertex of C is in C): bit (a, b)
+ * Dense core (a layout of the DAG; the paper has no counterpart). The build
+ * of a root u's first-level induced subgraph (Section 3.4) reads the out-list
+ * of every member of N+(u). The handle may also hold a bit matrix over a set
+ * C of the highest-ranked vertices: every vertex whose ranking key is at least
+ * a threshold, so that an out-neighbour of a vertex of C is in C. Bit (a, b)
  * is set iff C has the arc a -> b. The counting calls then take the row of a
  * member x of N+(u) from the matrix, one bit per later member of N+(u),
- * instead of scanning N+(x), where the out-list is the longer of the two
- * (kc_set_core_policy). Counts are the same with and without it. By default
- * it is built when the largest out-degree is at least 128 and the builds of
- * all roots would read, on average, at least 16 out-list entries per arc
- * (the sum over arcs u -> x of d+(x)), with at most
- * kc_set_core_policy's max_vertices vertices and a matrix no larger than
- * the DAG's arrays (64 MiB at least) and no larger than a quarter of the free
- * device memory; if its allocation fails the handle simply has no core.
+ * instead of scanning N+(x), where that reads less (kc_set_core_policy).
+ * Counts are the same with and without it.
+ * By default it is built when the largest out-degree is at least 128 and the
+ * builds of all roots would read on average at least 16 out-list entries per
+ * arc (the sum over arcs u -> x of d+(x)). Its size is at most
+ * kc_set_core_policy's max_vertices, its matrix at most the size of the DAG's
+ * arrays (64 MiB at least) and a quarter of the free device memory; if an
+ * allocation for it fails, the handle has no core. With KC_CORE_BITS it is
+ * always built (up to max_vertices) and a failed allocation gives KC_ENOMEM.
  * It costs |C|^2/8 bytes of device memory and one pass over the keys and the
- * core's arcs. With KC_CORE_BITS a failed allocation gives KC_ENOMEM.
+ * core's arcs.
  */
 kc_status kc_orient(const kc_csr *g, int method, kc_dag **out, kc_stream_t stream);
 

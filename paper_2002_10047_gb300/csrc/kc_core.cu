@@ -1,6 +1,7 @@
 // Dense-core adjacency of an oriented graph: a layout of the DAG, not a step
-// of the paper. The level-2 build of a root u (the DAG induced on N+(u),
-// Algorithm 1 / Section 3.2) reads the out-list of every member x of N+(u).
+// of the paper. The level-2 build of a root u (the DAG induced on N+(u), the
+// first-level induced subgraph of Section 3.4) reads the out-list of every
+// member x of N+(u).
 // On skewed graphs most of those reads are long out-lists of the few
 // highest-ranked vertices, reached from millions of light roots: on a
 // Chung-Lu graph the build scans sum over arcs u->x of d+(x), hundreds of
