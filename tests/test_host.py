@@ -55,3 +55,21 @@ def test_device_csr_builder_equals_host_csr():
     assert np.array_equal(rp.numpy().view(np.uint64), g.row_ptr)
     assert np.array_equal(col.numpy().view(np.uint32), g.col)
     del torch
+
+
+def test_bench_build_bytes_model():
+    """The bench's algorithmic bytes of a counting pass: without a dense core
+    the builds scan sum over arcs u->x of d+(x) entries (4 bytes each); with
+    one, the scanned entries plus one 64-bit word per core lookup plus the
+    members' core numbers (4 bytes per arc)."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench_model", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    n, m, head = 1000, 9000, 250000
+    plain = {"build_scanned": head, "build_lookups": 0, "core_vertices": 0}
+    assert bench.build_bytes(n, m, plain) == 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * head
+    core = {"build_scanned": 40000, "build_lookups": 3000, "core_vertices": 128}
+    assert bench.build_bytes(n, m, core) == 8 * (n + 1) + 4 * n + 4 * m + 8 * m + 4 * 40000 + 8 * 3000 + 4 * m
