@@ -23,6 +23,7 @@
 
 #include "kc_core.cuh"
 #include "kc_host.cuh"
+#include "kc_orient.cuh"
 
 namespace kc {
 
@@ -79,6 +80,20 @@ __global__ void core_assign_kernel(const uint64_t *__restrict__ key, uint32_t n,
     at = __shfl_sync(0xffffffffu, at, 0) + (unsigned)__popc(m & ((1u << lane_of()) - 1u));
     if (v < n) core_id[v] = in ? at : kNoCore;
   }
+}
+
+// cv[core_id[v]] = v for the core vertices
+__global__ void core_list_kernel(const uint32_t *__restrict__ core_id, uint32_t n, uint32_t *__restrict__ cv) {
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t a = core_id[v];
+    if (a != kNoCore) cv[a] = (uint32_t)v;
+  }
+}
+
+// core_id[cv[i]] = i: core numbers in rank order
+__global__ void core_renumber_kernel(const uint32_t *__restrict__ cv, uint32_t h, uint32_t *__restrict__ core_id) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < h; i += (size_t)gridDim.x * blockDim.x)
+    core_id[cv[i]] = (uint32_t)i;
 }
 
 // B[a][b] for every arc a -> b between core vertices: one warp per vertex,
@@ -275,6 +290,27 @@ kc_status build_core_impl(kc_dag *D, const uint64_t *rp, const uint64_t *key, in
     cudaFreeAsync(D->core_id, s);
     D->core_id = nullptr;
     return H == 0 ? KC_OK : internal_fail("dense core: more vertices above the threshold than selected");
+  }
+  // number the core in rank order, so that the later members of a root (in
+  // rank order) have increasing core numbers and the lookups of one row fall
+  // into few words: the core vertices as one row sorted by (key, id)
+  if (H > 1) {
+    DevBuf cv, rptr, rord;
+    KC_CK(cv.alloc(sizeof(uint32_t) * H, s));
+    KC_CK(rptr.alloc(sizeof(uint64_t) * 2, s));
+    KC_CK(rord.alloc(sizeof(uint32_t), s));
+    const uint64_t hp[2] = {0, H};
+    KC_CK(cudaMemcpyAsync(rptr.p, hp, sizeof hp, cudaMemcpyHostToDevice, s));
+    KC_CK(cudaMemsetAsync(rord.p, 0, sizeof(uint32_t), s));
+    core_list_kernel<<<grid, kCoreBlock, 0, s>>>(D->core_id, n, cv.as<uint32_t>());
+    note_launch();
+    KC_CK(cudaGetLastError());
+    const uint32_t big = H > 1024 ? 1u : 0u, mid = H > 32 ? 1u : 0u;
+    KC_CK(launch_sort_rows(rptr.as<uint64_t>(), cv.as<uint32_t>(), key, rord.as<uint32_t>(), big, mid, 1u, H, s));
+    core_renumber_kernel<<<grid, kCoreBlock, 0, s>>>(cv.as<uint32_t>(), H, D->core_id);
+    note_launch();
+    KC_CK(cudaGetLastError());
+    KC_CK(cudaStreamSynchronize(s));  // hp is a host buffer read by the copy above
   }
   const uint32_t words = (H + 63u) / 64u;
   const size_t bytes = (size_t)H * words * 8;
